@@ -1,0 +1,329 @@
+"""Pins for the CPU oracle against mathematics that does not come from the oracle itself.
+
+Closed forms (circle eigenvalues from Graf's theorem, cylinder series), library routines
+(numpy.linalg.solve), exact integrals, polynomial exactness, brute-force direct sums, and
+limits stated by the paper (Sec. III-C: the zeroed self term perturbs the filtered
+operator by an amount that vanishes as the grid is refined).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import aim, dense, geometry, solve, special
+
+K = 2.0 * math.pi
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+# --------------------------------------------------------------------------------------
+# Green's function and quadrature rules
+# --------------------------------------------------------------------------------------
+def test_green_small_argument_expansion():
+    # H0^(2)(x) = 1 - j(2/pi)(ln(x/2) + gamma) + O(x^2 ln x)  (Abramowitz & Stegun 9.1.12-13)
+    x = np.array([1e-6, 1e-5, 1e-4])
+    expect = -0.25j * (1.0 - 1j * (2.0 / math.pi) * (np.log(x / 2.0) + special.EULER_GAMMA))
+    got = special.green(1.0, x)
+    assert np.max(np.abs(got - expect)) < 1e-7
+
+
+def test_green_is_outgoing_for_positive_time_convention():
+    # H0^(2)(x) ~ sqrt(2/(pi x)) exp(-j(x - pi/4)) (1 + j/(8x)) for large x (A&S 9.2.4)
+    x = np.array([500.0, 1000.0])
+    h2 = np.sqrt(2.0 / (math.pi * x)) * np.exp(-1j * (x - math.pi / 4.0)) * (1.0 + 1j / (8.0 * x))
+    assert np.max(np.abs(special.green(1.0, x) - (-0.25j) * h2) / np.abs(h2)) < 1e-6
+
+
+@pytest.mark.parametrize("n", [2, 4, 8, 14])
+def test_gauss01_polynomial_exactness(n):
+    x, w = special.gauss01(n)
+    for d in range(2 * n):
+        assert abs(np.sum(w * x ** d) - 1.0 / (d + 1)) < 1e-14
+
+
+@pytest.mark.parametrize("b", [0, 1, 2, 5])
+def test_graded_rule_log_moments(b):
+    x, w = special.graded01()
+    assert abs(np.sum(w * x ** b * np.log(x)) + 1.0 / (b + 1) ** 2) < 1e-13
+
+
+# --------------------------------------------------------------------------------------
+# Interpolation Lambda (Sec. III-A)
+# --------------------------------------------------------------------------------------
+@pytest.mark.parametrize("s", [2, 3, 4, 5, 6, 10, 11])
+def test_lagrange_reproduces_polynomials(s):
+    rng = np.random.default_rng(s)
+    xi = rng.uniform(20.0, 30.0, 50)
+    base, w = aim.lagrange_1d(xi, s)
+    nodes = base[:, None] + np.arange(s)[None, :]
+    assert np.all(xi >= nodes[:, 0] - 1e-12) and np.all(xi <= nodes[:, -1] + 1e-12)
+    for d in range(s):
+        assert np.max(np.abs(np.sum(w * (nodes - 25.0) ** d, axis=1) - (xi - 25.0) ** d)) < 1e-9 * 5.0 ** d
+
+
+def test_stencils_2d_reproduce_bilinear_products():
+    rng = np.random.default_rng(1)
+    pts = rng.uniform(-0.9, 0.9, (40, 2))
+    L, m, s = 1.0, 33, 4
+    eps = aim.grid_spacing(L, m)
+    ix0, iy0, W = aim.stencils(pts, L, eps, s)
+    a = np.arange(s)
+    gx = -L + eps * (ix0[:, None] + a[None, :])
+    gy = -L + eps * (iy0[:, None] + a[None, :])
+    for px in range(s):
+        for py in range(s):
+            val = np.einsum("qba,qa,qb->q", W, gx ** px, gy ** py)
+            assert np.max(np.abs(val - pts[:, 0] ** px * pts[:, 1] ** py)) < 1e-12
+
+
+def test_grid_encloses_all_stencils():
+    nodes = synth.StarContour.from_seed(3).polygon(20.0, 200)
+    for m, s in ((32, 4), (64, 6), (40, 5)):
+        L = aim.grid_half_side(nodes, m, s)
+        eps = aim.grid_spacing(L, m)
+        r, _, _ = geometry.gauss_nodes(nodes, 4)
+        ix0, iy0, _ = aim.stencils(r, L, eps, s)
+        assert ix0.min() >= 0 and iy0.min() >= 0
+        assert ix0.max() + s - 1 <= m - 1 and iy0.max() + s - 1 <= m - 1
+
+
+# --------------------------------------------------------------------------------------
+# Dense exact operators (Eqs. 2-4) against the circle's closed forms
+# --------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def circle_dense():
+    out = {}
+    for n in (128, 256):
+        nodes = synth.circle_polygon(1.0, n)
+        S, N = dense.te_dense(nodes, K)
+        out[n] = (nodes, S, N, geometry.gram_dense(nodes))
+    return out
+
+
+def _modal(A, G, n, N):
+    v = np.exp(1j * n * 2.0 * math.pi * np.arange(N) / N)
+    return (A[0] @ v) / (G[0] @ v)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 3, 6, 10])
+def test_dense_S_N_circle_eigenvalues(circle_dense, mode):
+    # circulant on a regular polygon; O(h^2) discretisation error removed by Richardson
+    vals = {}
+    for n, (_, S, N, G) in circle_dense.items():
+        vals[n] = (_modal(S, G, mode, n), _modal(N, G, mode, n))
+    lam = (4 * vals[256][0] - vals[128][0]) / 3
+    mu = (4 * vals[256][1] - vals[128][1]) / 3
+    tol = 2e-4 if mode < 10 else 5e-4          # O(h^4) remainder grows with the mode number
+    assert abs(lam - special.circle_lambda(mode, K, 1.0)) / abs(special.circle_lambda(mode, K, 1.0)) < tol
+    assert abs(mu - special.circle_mu(mode, K, 1.0)) / abs(special.circle_mu(mode, K, 1.0)) < tol
+
+
+def test_dense_operators_are_complex_symmetric(circle_dense):
+    nodes = synth.StarContour.from_seed(5).polygon(6.0, 90)
+    S, N = dense.te_dense(nodes, K)
+    assert np.abs(S - S.T).max() < 1e-13 * np.abs(S).max()
+    assert np.abs(N - N.T).max() < 1e-13 * np.abs(N).max()
+
+
+def test_calderon_product_tends_to_quarter():
+    # lambda_n mu_n -> 1/4 for large n (Calderon identity for the closed forms)
+    n = np.array([20, 40, 100])
+    prod = special.circle_lambda(n, K, 1.0) * special.circle_mu(n, K, 1.0)
+    assert np.max(np.abs(prod - 0.25)) < 1e-3
+
+
+def test_discrete_calderon_eigenvalues(circle_dense):
+    nodes, S, N, G = circle_dense[256]
+    A = np.linalg.solve(G, S) @ np.linalg.solve(G, N)
+    v = np.exp(1j * 4 * 2.0 * math.pi * np.arange(256) / 256)
+    ray = np.vdot(v, A @ v) / np.vdot(v, v)
+    expect = special.circle_lambda(4, K, 1.0) * special.circle_mu(4, K, 1.0)
+    assert abs(ray - expect) / abs(expect) < 5e-3
+
+
+def test_singular_quadrature_converged():
+    nodes = synth.StarContour.from_seed(2).polygon(8.0, 80)
+    rows = np.array([0, 0, 0, 5, 17, 40])
+    cols = np.array([0, 1, 79, 7, 17, 43])
+    S1, N1 = dense.te_entries(nodes, K, rows, cols)
+    S2, N2 = dense.te_entries(nodes, K, rows, cols, n_close=20, n_far=12, levels=40, n_graded=18, n_y=22)
+    assert np.max(np.abs(S1 - S2) / np.abs(S2)) < 1e-12
+    assert np.max(np.abs(N1 - N2) / np.abs(N2)) < 1e-12
+    z1 = dense.tm_point_segment(nodes, K, rows, cols)
+    z2 = dense.tm_point_segment(nodes, K, rows, cols, n_close=24, n_far=12, levels=40, n_graded=18)
+    assert np.max(np.abs(z1 - z2) / np.abs(z2)) < 1e-12
+
+
+def test_gram_entries_exact():
+    nodes = synth.StarContour.from_seed(4).polygon(3.0, 30)
+    _, h, _, _ = geometry.segments(nodes)
+    G = geometry.gram_dense(nodes)
+    # <phi_i, phi_i> = (h_{i-1}+h_i)/3 ; <phi_i, phi_{i+1}> = h_i/6, by 3-point Gauss (exact for quadratics)
+    x, w = special.gauss01(3)
+    for i in (0, 7, 29):
+        diag = h[i] * np.sum(w * (1 - x) ** 2) + h[i - 1] * np.sum(w * x ** 2)
+        off = h[i] * np.sum(w * (1 - x) * x)
+        assert abs(G[i, i] - diag) < 1e-15 and abs(G[i, (i + 1) % 30] - off) < 1e-15
+
+
+@pytest.mark.parametrize("form", ["tm", "te"])
+def test_dense_solution_matches_cylinder_series(form):
+    N = 256
+    nodes = synth.circle_polygon(1.0, N)
+    if form == "tm":
+        Z = dense.tm_dense(nodes, K)
+        J = np.linalg.solve(Z, dense.tm_rhs(nodes, K, 0.0))
+        phi = 2 * math.pi * (np.arange(N) + 0.5) / N
+        ref = special.tm_cylinder_current(phi, K, 1.0)
+    else:
+        _, Nm = dense.te_dense(nodes, K)
+        J = np.linalg.solve(Nm, dense.te_rhs(nodes, K, 0.0))
+        phi = 2 * math.pi * np.arange(N) / N
+        ref = special.te_cylinder_current(phi, K, 1.0)
+    assert rel(J, ref) < 5e-3
+
+
+# --------------------------------------------------------------------------------------
+# AIM operators (Eqs. 7, 8, 10) and the numerical filter (Sec. III-B)
+# --------------------------------------------------------------------------------------
+@pytest.mark.parametrize("m,P", [(12, 24), (12, 23), (16, 64)])
+def test_fft_grid_product_equals_direct_toeplitz_sum(m, P):
+    u = synth.random_grid(m, 1, seed=m + P)[0]
+    eps = 0.05
+    c = aim.grid_kernel(K, eps, P)
+    # brute force: the Toeplitz matrix of grid-point interactions, self term zero (Sec. III-C)
+    iy, ix = np.divmod(np.arange(m * m), m)
+    r = eps * np.hypot(iy[:, None] - iy[None, :], ix[:, None] - ix[None, :])
+    T = np.where(r > 0, special.green(K, np.where(r > 0, r, 1.0)), 0.0)
+    brute = (T @ u.ravel()).reshape(m, m)
+    Chat = aim.dft2(c, direct=True)
+    assert rel(aim.conv_fft(u, Chat), brute) < 1e-13
+
+
+def test_unfiltered_product_independent_of_embedding_size():
+    nodes = synth.StarContour.from_seed(1).polygon(4.0, 48)
+    x = synth.random_coeffs(48, 1, 9)[0]
+    a = aim.TEOperators(nodes, K, 24, 48, near=False).S(x)
+    b = aim.TEOperators(nodes, K, 24, 128, near=False).S(x)
+    assert rel(a, b) < 1e-13
+    fa = aim.TEOperators(nodes, K, 24, 48, alpha=2 * K, near=False).S_alpha(x)
+    fb = aim.TEOperators(nodes, K, 24, 128, alpha=2 * K, near=False).S_alpha(x)
+    assert rel(fa, fb) > 1e-6          # the filtered operator depends on P (documented reading)
+
+
+@pytest.fixture(scope="module")
+def star_small():
+    nodes = synth.StarContour.from_seed(0).polygon(5.0, 64)
+    return nodes, aim.TEOperators(nodes, K, 32, 64, alpha=4 * K), aim.TMOperators(nodes, K, 32, 64, alpha=4 * K)
+
+
+def test_aim_fft_path_equals_direct_path(star_small):
+    nodes, te, tm = star_small
+    x = synth.random_coeffs(len(nodes), 2, 1)
+    for f in (te.S, te.S_alpha, te.N, tm.Z, tm.Z_alpha):
+        assert rel(f(x, method="fft"), f(x, method="direct")) < 1e-12
+
+
+def test_near_correction_makes_near_entries_exact(star_small):
+    nodes, te, tm = star_small
+    n = len(nodes)
+    S_aim = solve.assemble(te.S, n)
+    N_aim = solve.assemble(te.N, n)
+    S_ex, N_ex = dense.te_dense(nodes, K)
+    i, j = te.near_rows, te.near_cols
+    assert np.max(np.abs(S_aim[i, j] - S_ex[i, j])) < 1e-12 * np.abs(S_ex).max()
+    assert np.max(np.abs(N_aim[i, j] - N_ex[i, j])) < 1e-12 * np.abs(N_ex).max()
+    Z_aim = solve.assemble(tm.Z, n)
+    Z_ex = dense.tm_dense(nodes, K)
+    assert np.max(np.abs(Z_aim[tm.near_rows, tm.near_cols] - Z_ex[tm.near_rows, tm.near_cols])) < 1e-12 * np.abs(Z_ex).max()
+
+
+def test_unfiltered_aim_converges_to_dense():
+    nodes = synth.circle_polygon(1.0, 128)
+    S_ex, N_ex = dense.te_dense(nodes, K)
+    x = synth.random_coeffs(128, 1, 2)[0]
+    errs = []
+    for m in (24, 48):
+        op = aim.TEOperators(nodes, K, m, 2 * m)
+        errs.append((rel(op.S(x), S_ex @ x), rel(op.N(x), N_ex @ x)))
+    assert errs[1][0] < 0.5 * errs[0][0] and errs[1][1] < 0.5 * errs[0][1]
+    assert errs[1][0] < 1e-3 and errs[1][1] < 1e-3
+
+
+def test_filter_is_identity_above_grid_nyquist():
+    nodes = synth.StarContour.from_seed(6).polygon(4.0, 48)
+    op = aim.TEOperators(nodes, K, 24, 48, near=False)
+    big = aim.TEOperators(nodes, K, 24, 48, alpha=math.sqrt(2.0) * math.pi / op.eps * 1.0001, near=False)
+    x = synth.random_coeffs(48, 1, 4)[0]
+    assert rel(big.S_alpha(x), op.S(x)) < 1e-14
+    assert np.array_equal(big.mask & big.mask, big.mask) and big.mask.all()
+
+
+def test_zeroed_self_term_gives_zero_mean_spectrum():
+    c = aim.grid_kernel(K, 0.07, 32)
+    assert c[0, 0] == 0.0
+    Chat = aim.dft2(c, direct=True)
+    assert abs(Chat.sum()) < 1e-11 * np.abs(Chat).max() * 32
+
+
+@pytest.fixture(scope="module")
+def circle_filtered():
+    N = 256
+    nodes = synth.circle_polygon(1.0, N)
+    G = geometry.gram_dense(nodes)
+    ops = {m: aim.TEOperators(nodes, K, m, 2 * m, alpha=8 * K, near=False, direct_dft=False) for m in (64, 128, 256)}
+    return N, G, ops
+
+
+def _modal_op(apply, G, n, N):
+    v = np.exp(1j * n * 2.0 * math.pi * np.arange(N) / N)
+    return np.vdot(v, apply(v)) / np.vdot(v, G @ v)
+
+
+@pytest.mark.parametrize("mode", [0, 5, 10])
+def test_numerical_filter_converges_to_analytic_filter(circle_filtered, mode):
+    # Sec. III-C: zeroing the self cell perturbs the filtered spectrum by an amount that
+    # vanishes with eps; the numerical filter must approach Eq. 6's closed form.
+    N, G, ops = circle_filtered
+    exact = special.circle_lambda_filtered(mode, K, 1.0, 8 * K)
+    errs = [abs(_modal_op(ops[m].S_alpha, G, mode, N) - exact) / abs(exact) for m in (64, 128, 256)]
+    assert errs[1] < 0.45 * errs[0] and errs[2] < 0.45 * errs[1]
+    assert errs[2] < 2e-2
+
+
+def test_numerical_filter_truncates_beyond_alpha_a(circle_filtered):
+    # Fig. 2's statement: the filtered spectrum decays exponentially after the filtering point n ~ alpha a
+    N, G, ops = circle_filtered
+    op = ops[128]
+    low = abs(_modal_op(op.S_alpha, G, 20, N))
+    high = [abs(_modal_op(op.S_alpha, G, n, N)) for n in (70, 80, 90)]
+    unf = abs(special.circle_lambda(80, K, 1.0))
+    assert max(high) < 1e-3 * unf and low > 0.3 * abs(special.circle_lambda(20, K, 1.0))
+
+
+# --------------------------------------------------------------------------------------
+# Solvers
+# --------------------------------------------------------------------------------------
+def test_gmres_matches_dense_solve():
+    rng = np.random.default_rng(0)
+    n = 80
+    A = 3 * np.eye(n) + (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / math.sqrt(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    x, it, hist = solve.gmres(lambda v: A @ v, b, tol=1e-12, restart=15)
+    assert rel(x, np.linalg.solve(A, b)) < 1e-10 and hist[-1] < 1e-11
+
+
+def test_aim_calderon_solution_matches_series():
+    N = 256
+    nodes = synth.circle_polygon(1.0, N)
+    op = aim.TEOperators(nodes, K, 64, 128, alpha=8 * K)
+    E = dense.te_rhs(nodes, K, 0.0)
+    b = op.gram_solve(op.S(op.gram_solve(E)))
+    x, it, _ = solve.gmres(lambda v: op.calderon(v, filtered=False), b, tol=1e-10, restart=60)
+    ref = special.te_cylinder_current(2 * math.pi * np.arange(N) / N, K, 1.0)
+    assert rel(x, ref) < 5e-3
+    assert it < 40
