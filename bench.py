@@ -1,0 +1,356 @@
+#!/usr/bin/env python3
+"""Benchmark: filtered-AIM Calderon TE-EFIE solves on GB300.
+
+One step is one pass of the whole method for one scatterer: setup of every operator from the
+contour (quadrature, grid, projections, kernel spectrum and its circular truncation, near
+field, Gram inverse), the plane-wave excitation, and the GMRES solve of the filtered
+Calderon system G^-1 S^alpha G^-1 N j = G^-1 S^alpha G^-1 E to a relative residual of 1e-8.
+Workload: a seeded random smooth contour of perimeter 1000 wavelengths, 10 segments per
+wavelength (N = 10000), a 2048 x 2048 grid (P = 4096), 4 x 4 stencils, alpha = 2k, one
+right-hand side. Inputs are synthetic (no dataset exists for this workload).
+
+Under torchrun each rank solves its own contour (seed = rank): weak scaling, no collective in
+the data path; value = all ranks' solves / max-over-ranks time.
+
+--impl reference runs the CPU oracle (numpy/scipy FP64) on a bounded sample of the same
+workload on the host cores, rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "filtered AIM matvec HBM GB/s & solves/s at rel err<=1e-5; served p50/p99 latency"
+UNIT = "solves/s"
+SOLVE_TOL = 1e-8
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal GB300 FP64 rate)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seed", type=int, default=0)
+    return ap.parse_args()
+
+
+def workload(seed):
+    return synth.single_solve_scale(seed=seed)
+
+
+def workload_config(wl, precision, world):
+    return {"workload": "filtered Calderon TE-EFIE solve, perimeter 1000 wl, N=%d, grid %dx%d (P=%d), s=4, p=4, "
+                        "alpha=2k, 1 rhs, GMRES(50) tol %.0e" % (wl.n, wl.m, wl.m, wl.fft_P, SOLVE_TOL),
+            "N": wl.n, "grid_m": wl.m, "fft_P": wl.fft_P, "alpha_over_k": wl.alpha / wl.k, "nrhs": 1,
+            "precision": precision, "contour_seed": "rank", "ranks": world,
+            "l2": "inputs larger than L2 (grid intermediate 3 x 2048 x 4096 complex per product > 129 MB)"}
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sms.append(float(parts[1]))
+                    maxs.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, val in zip(names, parts[5:9]):
+                    if val.lower() == "active":
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sms:
+            return None
+        return {"sm_mhz": statistics.median(sms), "sm_max_mhz": max(maxs), "reasons": sorted(reasons),
+                "samples": len(sms)}
+
+
+def col_conv_algorithmic(wl, info, precision, channels):
+    """Algorithmic work of one column-pass launch (the dominant kernel).
+
+    Bytes: each channel's m_rows x P intermediate read once and written once, plus the stored
+    (P/2+1)^2 spectrum read once per launch. Flops (5 n log2 n per complex n-point FFT): per
+    column and channel four half-length FFTs, the twiddle of the odd half, the spectral
+    product of P points and the recombination of the kept rows.
+    """
+    P = wl.fft_P
+    H = P // 2
+    rows = info["row_hi"] - info["row_lo"] + 1
+    b = 16 if precision == "fp64" else 8
+    bytes_ = channels * 2 * rows * P * b + (H + 1) ** 2 * b
+    per_col = 4 * 5 * H * math.log2(H) + 6 * rows + 6 * P + 8 * rows
+    flops = channels * P * per_col
+    return bytes_, flops
+
+
+def gb300_arm(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_10784_gb300 import aim
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    prec = aim.FP64 if args.precision == "fp64" else aim.MIXED
+    wl = workload(args.seed + rank)
+    rhs = torch.empty((1, wl.n), dtype=torch.complex128, device=dev)
+    x = torch.zeros_like(rhs)
+    last = {}
+
+    def step():
+        ctx = aim.Context(wl.nodes, wl.k, aim.TE, wl.m, fft_P=wl.fft_P, alpha=wl.alpha)
+        ctx.rhs_planewave(wl.angles, rhs)
+        x.zero_()
+        info = ctx.solve("calderon_alpha", rhs, x, tol=SOLVE_TOL, restart=50, max_iter=2000, precision=prec,
+                         inner_tol=1e-4)
+        last["info"] = info[0]
+        last["ctx_info"] = ctx.info()
+        ctx.close()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    aim.profile_start()
+    l0 = aim.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    launches = aim.launch_count() - l0
+    prof = aim.profile_stop()
+    clocks = sampler.stop()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    value = args.steps * world / elapsed
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    rhs_h = torch.empty((1, wl.n), dtype=torch.complex128, pin_memory=True)
+    x_h = torch.empty((1, wl.n), dtype=torch.complex128, pin_memory=True)
+    with aim.Context(wl.nodes, wl.k, aim.TE, wl.m, fft_P=wl.fft_P, alpha=wl.alpha) as c0:
+        c0.rhs_planewave(wl.angles, rhs_h)
+
+    def step_e2e():
+        ctx = aim.Context(wl.nodes, wl.k, aim.TE, wl.m, fft_P=wl.fft_P, alpha=wl.alpha)
+        ctx.solve("calderon_alpha", rhs_h, x_h, tol=SOLVE_TOL, restart=50, max_iter=2000, precision=prec,
+                  inner_tol=1e-4)
+        ctx.close()
+
+    step_e2e()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_e2e()
+    torch.cuda.synchronize()
+    e2e_el = time.perf_counter() - t0
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_el], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_el = float(t.item())
+        dist.destroy_process_group()
+    e2e = {"value": args.steps * world / e2e_el, "unit": UNIT,
+           "h2d_bytes_per_step": int(wl.nodes.nbytes + rhs_h.numel() * 16),
+           "d2h_bytes_per_step": int(x_h.numel() * 16)}
+
+    if rank != 0:
+        return None
+    # roofline of the dominant kernel (largest total time in the timed region)
+    peaks, src = load_peaks()
+    top = max(prof.items(), key=lambda kv: kv[1][1])
+    name, (nl, tms) = top
+    avg_s = tms / nl / 1e3
+    info = last["ctx_info"]
+    roof = None
+    if name.startswith("col_conv"):
+        # the Calderon product runs 3 channels (N) and 1 channel (S^alpha) per application
+        n_n = nl // 2
+        b3, f3 = col_conv_algorithmic(wl, info, args.precision, 3)
+        b1, f1 = col_conv_algorithmic(wl, info, args.precision, 1)
+        per_launch_bytes = (b3 + b1) / 2
+        per_launch_flops = (f3 + f1) / 2
+        if args.precision == "fp64":
+            ach = per_launch_flops / avg_s / 1e12
+            roof = {"bound": "alu", "kernel": name, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                    "peak_source": "FP64 nominal: 152 SMs x 64 FP64 flop/clk x 2.07 GHz (MEASURED_PEAKS has no FP64)",
+                    "algorithmic_bytes_per_launch": per_launch_bytes,
+                    "hbm_frac_of_measured": per_launch_bytes / avg_s / 1e9 / peaks["hbm_gbs"],
+                    "launches": nl, "avg_launch_ms": avg_s * 1e3}
+        else:
+            ach = per_launch_bytes / avg_s / 1e9
+            roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                    "launches": nl, "avg_launch_ms": avg_s * 1e3}
+    kernels = {k: {"launches": v[0], "total_ms": round(v[1], 3)} for k, v in prof.items()}
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": max(3, args.warmup), "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "c128" if args.precision == "fp64" else "c64+f64",
+           "data": "synthetic (seeded random smooth contour family)",
+           "config": workload_config(wl, args.precision, world), "e2e": e2e, "gpu_launches": launches,
+           "roofline": roof, "clocks": clocks, "solve": last["info"],
+           "setup_seconds_lib": last["ctx_info"]["setup_seconds"], "kernels": kernels}
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(wl, last["info"]["iters"])
+    return out
+
+
+# --------------------------------------------------------------------------------------
+# CPU oracle (baseline leg and reference arm)
+# --------------------------------------------------------------------------------------
+def oracle_sample(wl, iters, n_near_rows=64, n_matvec=1):
+    """Times the oracle on a bounded sample of one solve and extrapolates to solves/s.
+
+    Sample: the oracle's grid kernel + spectrum (full size), projections (full size), the
+    near-field correction for `n_near_rows` rows scaled to N rows, and `n_matvec` filtered
+    Calderon products; solve time = setup + iters x product time, iters = the GPU solve's
+    GMRES iteration count.
+    """
+    from oracle import aim as oaim
+    t0 = time.perf_counter()
+    op = oaim.TEOperators(wl.nodes, wl.k, wl.m, wl.fft_P, alpha=wl.alpha, near=False, direct_dft=False)
+    t_grid = time.perf_counter() - t0
+    rows = np.arange(0, wl.n, max(1, wl.n // n_near_rows))[:n_near_rows]
+    t1 = time.perf_counter()
+    op._near_setup(rows=rows)
+    t_near = (time.perf_counter() - t1) * wl.n / len(rows)
+    x = synth.random_coeffs(wl.n, 1, 5)[0]
+    t2 = time.perf_counter()
+    for _ in range(n_matvec):
+        op.calderon(x, filtered=True)
+    t_mv = (time.perf_counter() - t2) / n_matvec
+    solve_s = t_grid + t_near + iters * t_mv
+    return {"value": 1.0 / solve_s, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "oracle setup (grid kernel, spectrum, projections) at full size + near field on %d of %d rows "
+                      "scaled + %d filtered Calderon product(s); solve = setup + %d x product" %
+                      (len(rows), wl.n, n_matvec, iters),
+            "seconds": {"grid_setup": t_grid, "near_field_scaled": t_near, "calderon_product": t_mv}}
+
+
+GPU_ITERS_HINT = 30   # GMRES iterations of the GPU solve of this workload (used by the reference arm)
+
+
+def cpu_baseline(wl, iters):
+    return oracle_sample(wl, iters)
+
+
+def reference_arm(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    wl = workload(args.seed)
+    times = []
+    res = None
+    for i in range(max(3, args.warmup) + args.steps):
+        t0 = time.perf_counter()
+        res = oracle_sample(wl, GPU_ITERS_HINT, n_near_rows=16, n_matvec=1)
+        if i >= max(3, args.warmup):
+            times.append(1.0 / res["value"])
+    value = len(times) / sum(times)
+    base = dict(res)
+    base["value"] = value
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": 1e3 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128", "data": "synthetic (seeded random smooth contour family)",
+            "config": workload_config(wl, "fp64", world), "cpu_baseline": base,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+
+
+def main():
+    args = parse()
+    out = reference_arm(args) if args.impl == "reference" else gb300_arm(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

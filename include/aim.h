@@ -1,0 +1,234 @@
+/*
+ * aim.h - C ABI of the GB300 library for the numerically filtered Adaptive Integral Method
+ * (AIM) applied to the 2-D electric field integral equation (EFIE).
+ *
+ * Method: T. Pignatelli, V. Giunzioni, P. Ricci, M. E. Masciocchi, A. Merlini,
+ * F. P. Andriulli, "A Numerical Approach to Operator Filtering within the Adaptive
+ * Integral Method for Electromagnetic Integral Equations".
+ *
+ * What the library computes (section / equation of that paper):
+ *   - TE-EFIE operators on a closed curve with piecewise-linear hats and Galerkin testing
+ *     (Sec. II, Eqs. 1-4): the single layer S, the hypersingular N, the Gram matrix G,
+ *     and the Calderon-preconditioned operator G^-1 S G^-1 N (Eq. 3);
+ *   - their AIM matrix-vector products (Sec. III-A, Eqs. 7-8): projection of the
+ *     quadrature nodes onto a uniform m x m grid, circulant embedding of the grid kernel,
+ *     an FFT product, and interpolation back;
+ *   - the numerically filtered S^alpha (Sec. III-B, Eq. 10): the kernel spectrum F(c_grid)
+ *     truncated to the disc |kappa| <= alpha, with the grid self term set to zero
+ *     (Sec. III-C);
+ *   - the TM-EFIE (pulse basis, midpoint collocation) single-layer system on the same
+ *     grid machinery, filtered or not;
+ *   - GMRES solves of these systems (the paper's "iterative solvers", Sec. I).
+ * Unfiltered operators carry a sparse near-field correction (exact singular quadrature
+ * minus the AIM entry for close pairs); the paper itself only zeroes the grid self term.
+ *
+ * Conventions
+ *   - Lengths and the wavenumber k share one unit; time dependence e^{+j w t};
+ *     g(r) = -(j/4) H0^(2)(k r); eta = 1.
+ *   - Complex vectors are interleaved (re, im). precision 0 (AIM_FP64): complex128;
+ *     precision 1 (AIM_MIXED): the grid FFT products and the near-field SpMV run in
+ *     complex64 while the vectors a caller passes stay complex128.
+ *   - Multi-vector arguments are column-major: vector r of nrhs starts at element r*n.
+ *   - Vector pointers may be device memory or host memory (pageable or pinned); the
+ *     library detects which (cudaPointerGetAttributes) and stages host data through
+ *     its own device buffers on the call's stream. The caller keeps ownership.
+ *   - `stream` is a cudaStream_t (NULL: the legacy default stream). Calls return after
+ *     enqueueing device work unless stated otherwise; results in host memory are
+ *     complete when the call returns.
+ *   - Every entry point returns a status; none exits, traps or aborts. A one-line reason
+ *     for the last failure on the calling thread is returned by aim_last_error().
+ *   - Calls on one context must not overlap (no internal locking); different contexts may
+ *     be used concurrently from different threads and streams.
+ */
+#ifndef AIM_GB300_H
+#define AIM_GB300_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  AIM_OK = 0,
+  AIM_EINVAL = 1,    /* an argument is out of range or inconsistent */
+  AIM_ENOMEM = 2,    /* a device or host allocation failed, or a memory budget was exceeded */
+  AIM_ECUDA = 3,     /* a CUDA runtime call failed */
+  AIM_ENOCONV = 4,   /* GMRES reached max_iter without meeting the tolerance */
+  AIM_ENUMERIC = 5,  /* a non-finite value appeared (NaN/Inf in inputs or residuals) */
+  AIM_ETIMEOUT = 6,  /* the solve exceeded its time limit */
+  AIM_ESTATE = 7     /* the call does not apply to this context (e.g. TE operator on a TM context) */
+} aim_status;
+
+typedef enum {
+  AIM_TM_PULSE_COLLOC = 0,  /* TM-EFIE: pulse basis per segment, collocation at segment midpoints */
+  AIM_TE_P1_GALERKIN = 1    /* TE-EFIE: P1 hat per vertex, Galerkin testing (Sec. II) */
+} aim_form;
+
+typedef enum {
+  AIM_OP_S = 0,               /* single layer S (Eq. 4): AIM + near-field correction */
+  AIM_OP_S_ALPHA = 1,         /* numerically filtered S^alpha (Eq. 10), no correction */
+  AIM_OP_N = 2,               /* TE only: hypersingular N (Eq. 2) in Maue form, AIM + near field */
+  AIM_OP_CALDERON = 3,        /* TE only: G^-1 S G^-1 N (Eq. 3) */
+  AIM_OP_CALDERON_ALPHA = 4,  /* TE only: G^-1 S^alpha G^-1 N (Eq. 3 with Eq. 10) */
+  AIM_OP_GRAM_INV = 5,        /* TE only: G^-1 (G of Eq. 3) */
+  AIM_OP_EFIE = 6,            /* system matrix of the EFIE: TM j k eta S ; TE N (Eq. 1 scaled by jk/eta) */
+  AIM_OP_EFIE_ALPHA = 7       /* TM only: j k eta S^alpha */
+} aim_op;
+
+enum { AIM_FP64 = 0, AIM_MIXED = 1 };
+
+/* Geometry: a closed polygon, counter-clockwise, given by its n_seg vertices (x0,y0,x1,y1,...).
+ * Segment e joins vertex e to vertex e+1 (mod n_seg). The unknowns are one per segment (TM)
+ * or one per vertex (TE); either way there are n_seg of them. */
+typedef struct {
+  int n_seg;
+  const double* xy;   /* host pointer, 2*n_seg doubles; copied by aim_setup */
+  aim_form form;
+  int quad_p;         /* Gauss-Legendre nodes per segment used by the projections (Eq. 7), 1..16 */
+} aim_geometry;
+
+/* Grid (Sec. III-A): m points per side spanning [-L, L]^2, spacing eps = 2L/(m-1).
+ * half_side_L <= 0 selects L = R/(1-(s+2)/(m-1)), R = max |vertex coordinate|.
+ * fft_P is the circulant embedding side: 0 selects the smallest power of two >= 2m-1;
+ * otherwise it must be a power of two with 2m-1 <= fft_P <= 4096. */
+typedef struct {
+  int m;
+  double half_side_L;
+  int fft_P;
+} aim_grid;
+
+/* Interpolation stencil: s points per axis (Lagrange, 2..12); near_radius <= 0 selects s*eps.
+ * Hat (or segment) pairs whose supports come within near_radius get exact entries in the
+ * unfiltered operators. */
+typedef struct {
+  int s;
+  double near_radius;
+} aim_stencil;
+
+/* Filter (Sec. III-B): keep spectral bins with kappa <= alpha; requires alpha > k. */
+typedef struct {
+  int enabled;
+  double alpha;
+} aim_filter;
+
+typedef struct {
+  double tol;          /* relative residual target ||b - A x|| / ||b|| of the solved system */
+  int restart;         /* GMRES restart length (1..10000); the Krylov basis takes
+                          (restart+4) * n * nrhs * 16 bytes of device memory */
+  int max_iter;        /* total inner iterations per right-hand side */
+  int precision;       /* AIM_FP64 or AIM_MIXED (FP32 grid + FP64 iterative refinement) */
+  double inner_tol;    /* mixed only: relative tolerance of each inner FP32-grid solve (e.g. 1e-4) */
+  int timeout_ms;      /* <= 0: no limit */
+} aim_solve_opts;
+
+typedef struct {
+  int iters;           /* GMRES iterations (inner iterations summed over refinement steps) */
+  int outer_iters;     /* refinement steps (1 in FP64 mode) */
+  double rel_res;      /* final relative residual of the solved system, FP64 matvec */
+  int converged;       /* 1 if rel_res <= tol */
+} aim_solve_info;
+
+typedef struct {
+  int n;               /* unknowns */
+  int m, fft_P, s, quad_p;
+  double k, L, eps, alpha;
+  int n_active;        /* grid points touched by the projections */
+  int row_lo, row_hi;  /* grid rows holding active points */
+  long long nnz_near;  /* near-field correction entries */
+  size_t device_bytes; /* device memory held by the context */
+  double setup_seconds;
+} aim_info;
+
+typedef struct aim_ctx aim_ctx;
+
+/* Builds every operator of the context on the current CUDA device (Secs. II-III):
+ * quadrature nodes and hat values (Eq. 7), the grid and the projections P = Lambda W Phi
+ * (Sec. III-A), the grid kernel samples with the self term set to zero (Sec. III-C), its
+ * spectrum and the filtered spectrum (Sec. III-B), the near-field correction, and G.
+ * All inputs are host memory and are copied. Work runs on `stream`; the call
+ * synchronises it before returning. On success *out owns all device state until
+ * aim_destroy. Errors: AIM_EINVAL (n_seg < 3, m < 8, bad P, alpha <= k when enabled,
+ * s outside 2..12, quad_p outside 1..16, k <= 0, a vertex outside the grid),
+ * AIM_ENOMEM, AIM_ECUDA. */
+aim_status aim_setup(const aim_geometry* geometry, double k, const aim_grid* grid,
+                     const aim_stencil* stencil, const aim_filter* filter, void* stream,
+                     aim_ctx** out);
+
+/* Releases everything the context owns. NULL is allowed. */
+void aim_destroy(aim_ctx* ctx);
+
+aim_status aim_get_info(const aim_ctx* ctx, aim_info* info);
+
+/* Pre-allocates workspaces for up to nrhs simultaneous vectors in the given precision,
+ * so that later calls (and CUDA-graph capture of them) allocate nothing. */
+aim_status aim_reserve(aim_ctx* ctx, int nrhs, int precision);
+
+/* Right-hand sides for unit plane waves exp(-j k khat.r), khat = (cos th, sin th):
+ * TE: E_i = <phi_i, (jk/eta) E_t> with E^i = eta H^i_z (z x khat) (Sec. II, below Eq. 2);
+ * TM: E_i = E^i_z(midpoint_i). `angles` is a host array of nrhs angles (radians);
+ * `rhs` receives n*nrhs complex128 values (host or device). */
+aim_status aim_rhs_planewave(aim_ctx* ctx, int nrhs, const double* angles, void* rhs, void* stream);
+
+/* y = A x for nrhs vectors (complex128 in and out, n*nrhs each; host or device; x and y
+ * must not overlap). A is selected by `op` (see aim_op); precision selects the grid
+ * arithmetic. The work is the pipeline of Eq. 8 / Eq. 10: sparse anterpolation fused
+ * into a forward row FFT, a column FFT fused with the spectral product and the inverse
+ * column FFT, an inverse row FFT with restriction, and the interpolation gather fused
+ * with the near-field SpMV. Errors: AIM_EINVAL, AIM_ESTATE, AIM_ENOMEM, AIM_ECUDA. */
+aim_status aim_matvec(aim_ctx* ctx, aim_op op, int nrhs, const void* x, void* y,
+                      int precision, void* stream);
+
+/* The grid product alone (the bracket of Eq. 8, or of Eq. 10 when filtered != 0) on
+ * full m x m grids: v = [F^-1(F(c) .* F(b))]_restr with b = u zero-padded to P x P.
+ * u and v hold nrhs row-major m x m complex128 grids (element (iy, ix) at iy*m + ix);
+ * host or device. Rows of u outside the context's active row range must be zero; rows of
+ * v outside it are returned as zero. */
+aim_status aim_grid_product(aim_ctx* ctx, int filtered, int nrhs, const void* u, void* v,
+                            int precision, void* stream);
+
+/* Solves A x = b for nrhs right-hand sides by restarted GMRES with FP64 Arnoldi
+ * (classical Gram-Schmidt, applied twice). `system` is AIM_OP_EFIE, AIM_OP_EFIE_ALPHA,
+ * AIM_OP_CALDERON or AIM_OP_CALDERON_ALPHA. For the Calderon systems `rhs` is the EFIE
+ * excitation E and the solver forms G^-1 S G^-1 E itself (Eq. 3). In AIM_MIXED precision
+ * the inner GMRES uses the FP32 grid product and the outer loop refines with FP64
+ * residuals until opts->tol. x is both the initial guess (if x0_given != 0) and the
+ * result. info receives nrhs entries (host pointer, may be NULL).
+ * Returns AIM_ENOCONV, AIM_ETIMEOUT or AIM_ENUMERIC when any right-hand side fails. */
+aim_status aim_solve(aim_ctx* ctx, aim_op system, int nrhs, const void* rhs, void* x,
+                     int x0_given, const aim_solve_opts* opts, aim_solve_info* info,
+                     void* stream);
+
+/* Upper bound on the device bytes aim_setup + aim_reserve(nrhs, precision) would hold,
+ * without building anything (admission control). */
+aim_status aim_query_bytes(const aim_geometry* geometry, const aim_grid* grid,
+                           const aim_stencil* stencil, int nrhs, int precision, size_t* bytes);
+
+/* Launch accounting and kernel timing (no counterpart in the paper; for measurement).
+ * aim_launch_count: kernels the library has enqueued in this process so far (all contexts).
+ * aim_profile_start: from now on every launch is bracketed by two CUDA events recorded on
+ * its own stream (adds two event records per launch).
+ * aim_profile_stop: waits for the recorded events, writes per-kernel launch counts and
+ * summed durations (ms) for up to max_stats kernels into `stats` (host array), sets *count,
+ * and stops timing. `name` points to a static string. */
+typedef struct {
+  int kernel;
+  const char* name;
+  long long launches;
+  double total_ms;
+} aim_kernel_stat;
+
+long long aim_launch_count(void);
+aim_status aim_profile_start(void);
+aim_status aim_profile_stop(aim_kernel_stat* stats, int max_stats, int* count);
+
+const char* aim_status_str(aim_status status);
+
+/* Reason for the most recent failure on the calling thread ("" if none). */
+const char* aim_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AIM_GB300_H */

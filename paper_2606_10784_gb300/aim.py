@@ -1,0 +1,254 @@
+"""Python binding of the AIM C ABI (include/aim.h): argument marshalling only.
+
+Every step of setup, matrix-vector products and solves runs inside libaimgb300.so. There is
+no fallback: if the compiled library is missing this module raises on import of `lib()`.
+Vectors are complex128 with shape (nrhs, n) (row r is right-hand side r, matching the ABI's
+column-major n x nrhs layout); they may be torch tensors (CUDA or CPU) or numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libaimgb300.so")
+
+# enums (mirror include/aim.h)
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENUMERIC, ETIMEOUT, ESTATE = range(8)
+TM, TE = 0, 1
+OP_S, OP_S_ALPHA, OP_N, OP_CALDERON, OP_CALDERON_ALPHA, OP_GRAM_INV, OP_EFIE, OP_EFIE_ALPHA = range(8)
+FP64, MIXED = 0, 1
+
+OPS = {"S": OP_S, "S_alpha": OP_S_ALPHA, "N": OP_N, "calderon": OP_CALDERON,
+       "calderon_alpha": OP_CALDERON_ALPHA, "gram_inv": OP_GRAM_INV, "efie": OP_EFIE, "efie_alpha": OP_EFIE_ALPHA}
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("n_seg", ctypes.c_int), ("xy", ctypes.POINTER(ctypes.c_double)), ("form", ctypes.c_int),
+                ("quad_p", ctypes.c_int)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int), ("half_side_L", ctypes.c_double), ("fft_P", ctypes.c_int)]
+
+
+class Stencil(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_int), ("near_radius", ctypes.c_double)]
+
+
+class Filter(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_int), ("alpha", ctypes.c_double)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("precision", ctypes.c_int), ("inner_tol", ctypes.c_double), ("timeout_ms", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("rel_res", ctypes.c_double),
+                ("converged", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("m", ctypes.c_int), ("fft_P", ctypes.c_int), ("s", ctypes.c_int),
+                ("quad_p", ctypes.c_int), ("k", ctypes.c_double), ("L", ctypes.c_double), ("eps", ctypes.c_double),
+                ("alpha", ctypes.c_double), ("n_active", ctypes.c_int), ("row_lo", ctypes.c_int),
+                ("row_hi", ctypes.c_int), ("nnz_near", ctypes.c_longlong), ("device_bytes", ctypes.c_size_t),
+                ("setup_seconds", ctypes.c_double)]
+
+
+class KernelStat(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("name", ctypes.c_char_p), ("launches", ctypes.c_longlong),
+                ("total_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def launch_count() -> int:
+    """Kernels the library has enqueued in this process."""
+    return int(lib().aim_launch_count())
+
+
+def profile_start():
+    _check(lib().aim_profile_start(), "aim_profile_start")
+
+
+def profile_stop() -> dict:
+    """Per-kernel {name: (launches, total_ms)} since profile_start (waits for the events)."""
+    stats = (KernelStat * 32)()
+    cnt = ctypes.c_int(0)
+    _check(lib().aim_profile_stop(stats, 32, ctypes.byref(cnt)), "aim_profile_stop")
+    return {stats[i].name.decode(): (stats[i].launches, stats[i].total_ms) for i in range(cnt.value)}
+
+
+def lib() -> ctypes.CDLL:
+    """Load libaimgb300.so (built by __graft_entry__.build() or build.py)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libaimgb300.so is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    L.aim_setup.argtypes = [ctypes.POINTER(Geometry), d, ctypes.POINTER(Grid), ctypes.POINTER(Stencil),
+                            ctypes.POINTER(Filter), vp, ctypes.POINTER(vp)]
+    L.aim_setup.restype = i
+    L.aim_destroy.argtypes = [vp]
+    L.aim_destroy.restype = None
+    L.aim_get_info.argtypes = [vp, ctypes.POINTER(Info)]
+    L.aim_get_info.restype = i
+    L.aim_reserve.argtypes = [vp, i, i]
+    L.aim_reserve.restype = i
+    L.aim_rhs_planewave.argtypes = [vp, i, ctypes.POINTER(d), vp, vp]
+    L.aim_rhs_planewave.restype = i
+    L.aim_matvec.argtypes = [vp, i, i, vp, vp, i, vp]
+    L.aim_matvec.restype = i
+    L.aim_grid_product.argtypes = [vp, i, i, vp, vp, i, vp]
+    L.aim_grid_product.restype = i
+    L.aim_solve.argtypes = [vp, i, i, vp, vp, i, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
+    L.aim_solve.restype = i
+    L.aim_query_bytes.argtypes = [ctypes.POINTER(Geometry), ctypes.POINTER(Grid), ctypes.POINTER(Stencil), i, i,
+                                  ctypes.POINTER(ctypes.c_size_t)]
+    L.aim_query_bytes.restype = i
+    L.aim_launch_count.argtypes = []
+    L.aim_launch_count.restype = ctypes.c_longlong
+    L.aim_profile_start.argtypes = []
+    L.aim_profile_start.restype = i
+    L.aim_profile_stop.argtypes = [ctypes.POINTER(KernelStat), i, ctypes.POINTER(i)]
+    L.aim_profile_stop.restype = i
+    L.aim_status_str.argtypes = [i]
+    L.aim_status_str.restype = ctypes.c_char_p
+    L.aim_last_error.argtypes = []
+    L.aim_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+class AimError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        L = lib()
+        msg = "%s: %s (%s)" % (where, L.aim_status_str(status).decode(), L.aim_last_error().decode())
+        super().__init__(msg)
+        self.status = status
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise AimError(status, where)
+
+
+def _ptr(a) -> int:
+    """Raw pointer of a contiguous torch tensor or numpy array."""
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError("expected a torch tensor or numpy array")
+
+
+def _stream_ptr(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _geometry(nodes: np.ndarray, form: int, quad_p: int):
+    xy = np.ascontiguousarray(np.asarray(nodes, dtype=np.float64).reshape(-1))
+    g = Geometry(int(xy.size // 2), xy.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(form), int(quad_p))
+    return g, xy
+
+
+def query_bytes(nodes, form: int, m: int, s: int = 4, quad_p: int = 4, fft_P: int = 0, nrhs: int = 1,
+                precision: int = FP64) -> int:
+    g, keep = _geometry(nodes, form, quad_p)
+    out = ctypes.c_size_t(0)
+    _check(lib().aim_query_bytes(ctypes.byref(g), ctypes.byref(Grid(m, 0.0, fft_P)), ctypes.byref(Stencil(s, 0.0)),
+                                 nrhs, precision, ctypes.byref(out)), "aim_query_bytes")
+    return out.value
+
+
+class Context:
+    """One AIM operator set on the current CUDA device (wraps aim_ctx*)."""
+
+    def __init__(self, nodes, k: float, form: int, m: int, fft_P: int = 0, L: float = 0.0, s: int = 4,
+                 quad_p: int = 4, near_radius: float = 0.0, alpha: Optional[float] = None, stream=None):
+        g, keep = _geometry(nodes, form, quad_p)
+        flt = Filter(1 if alpha is not None else 0, float(alpha) if alpha is not None else 0.0)
+        h = ctypes.c_void_p()
+        _check(lib().aim_setup(ctypes.byref(g), float(k), ctypes.byref(Grid(int(m), float(L), int(fft_P))),
+                               ctypes.byref(Stencil(int(s), float(near_radius))), ctypes.byref(flt),
+                               _stream_ptr(stream), ctypes.byref(h)), "aim_setup")
+        self._h = h
+        self.form = form
+        inf = self.info()
+        self.n = inf["n"]
+        self.m = inf["m"]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().aim_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def info(self) -> dict:
+        inf = Info()
+        _check(lib().aim_get_info(self._h, ctypes.byref(inf)), "aim_get_info")
+        return {name: getattr(inf, name) for name, _ in Info._fields_}
+
+    def reserve(self, nrhs: int, precision: int = FP64):
+        _check(lib().aim_reserve(self._h, int(nrhs), int(precision)), "aim_reserve")
+
+    def rhs_planewave(self, angles, out, stream=None):
+        ang = np.ascontiguousarray(np.asarray(angles, dtype=np.float64).reshape(-1))
+        _check(lib().aim_rhs_planewave(self._h, int(ang.size), ang.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                       _ptr(out), _stream_ptr(stream)), "aim_rhs_planewave")
+        return out
+
+    def matvec(self, op, x, y, precision: int = FP64, stream=None):
+        op = OPS[op] if isinstance(op, str) else int(op)
+        nrhs = x.shape[0] if x.ndim == 2 else 1
+        _check(lib().aim_matvec(self._h, op, int(nrhs), _ptr(x), _ptr(y), int(precision), _stream_ptr(stream)),
+               "aim_matvec")
+        return y
+
+    def grid_product(self, u, v, filtered: bool, precision: int = FP64, stream=None):
+        nrhs = u.shape[0] if u.ndim == 3 else 1
+        _check(lib().aim_grid_product(self._h, int(bool(filtered)), int(nrhs), _ptr(u), _ptr(v), int(precision),
+                                      _stream_ptr(stream)), "aim_grid_product")
+        return v
+
+    def solve(self, system, rhs, x, tol=1e-8, restart=50, max_iter=1000, precision: int = FP64, inner_tol=1e-4,
+              timeout_ms=0, x0_given=False, stream=None, check=True):
+        system = OPS[system] if isinstance(system, str) else int(system)
+        nrhs = rhs.shape[0] if rhs.ndim == 2 else 1
+        opts = SolveOpts(float(tol), int(restart), int(max_iter), int(precision), float(inner_tol), int(timeout_ms))
+        infos = (SolveInfo * nrhs)()
+        st = lib().aim_solve(self._h, system, int(nrhs), _ptr(rhs), _ptr(x), int(bool(x0_given)), ctypes.byref(opts),
+                             infos, _stream_ptr(stream))
+        out = [{"iters": i.iters, "outer_iters": i.outer_iters, "rel_res": i.rel_res, "converged": i.converged}
+               for i in infos]
+        if check:
+            _check(st, "aim_solve")
+        return out if check else (st, out)

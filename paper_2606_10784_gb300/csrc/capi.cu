@@ -1,0 +1,481 @@
+// C ABI of the AIM library (declared in include/aim.h): context lifecycle, setup
+// orchestration, operator composition (Eq. 3), host/device pointer staging and the solve.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "aim_internal.h"
+
+namespace aim {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+aim_status fail(aim_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+aim_status dev_alloc(aim_ctx* ctx, void** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return AIM_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AIM_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  ctx->allocations.push_back(*p);
+  ctx->device_bytes += bytes;
+  return AIM_OK;
+}
+
+static bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+static int ilog2(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+static bool device_pointer(const void* p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+static aim_status grow(void** buf, size_t* have, size_t need) {
+  if (*have >= need) return AIM_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc(buf, need);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AIM_ENOMEM, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  *have = need;
+  return AIM_OK;
+}
+
+aim_status reserve(aim_ctx* ctx, int nrhs, int precision) {
+  if (nrhs < 1) return fail(AIM_EINVAL, "nrhs must be >= 1");
+  const int pidx = precision == AIM_MIXED ? 1 : 0;
+  const int chan = (ctx->form == AIM_TE_P1_GALERKIN ? 3 : 1) * nrhs;
+  const size_t el = precision == AIM_MIXED ? sizeof(float2) : sizeof(double2);
+  AIM_TRY(grow(&ctx->inter, &ctx->inter_bytes, inter_bytes_needed(ctx, chan, precision)));
+  AIM_TRY(grow(&ctx->vact, &ctx->vact_bytes, (size_t)chan * ctx->n_act * el));
+  void* vw = ctx->vec_ws;
+  AIM_TRY(grow(&vw, &ctx->vec_ws_bytes, 2 * (size_t)nrhs * ctx->n * sizeof(double2)));
+  ctx->vec_ws = static_cast<double2*>(vw);
+  ctx->reserved_rhs[pidx] = std::max(ctx->reserved_rhs[pidx], nrhs);
+  return AIM_OK;
+}
+
+static aim_status stage(aim_ctx* ctx, size_t in_bytes, size_t out_bytes) {
+  const size_t need = std::max(in_bytes, out_bytes);
+  if (ctx->stage_bytes < need) {
+    if (ctx->stage_in) cudaFree(ctx->stage_in);
+    if (ctx->stage_out) cudaFree(ctx->stage_out);
+    ctx->stage_in = ctx->stage_out = nullptr;
+    ctx->stage_bytes = 0;
+    void* a = nullptr;
+    void* b = nullptr;
+    AIM_CUDA_TRY(cudaMalloc(&a, need));
+    cudaError_t e = cudaMalloc(&b, need);
+    if (e != cudaSuccess) {
+      cudaFree(a);
+      return fail(AIM_ENOMEM, "staging buffer");
+    }
+    ctx->stage_in = static_cast<double2*>(a);
+    ctx->stage_out = static_cast<double2*>(b);
+    ctx->stage_bytes = need;
+  }
+  return AIM_OK;
+}
+
+static PassSpec make_spec(const aim_ctx* ctx, aim_op op) {
+  PassSpec s{};
+  s.out_scale = double2{1.0, 0.0};
+  const double k2 = ctx->k * ctx->k;
+  switch (op) {
+    case AIM_OP_N:
+      s.nproj = 3;
+      s.proj[0] = 1; s.proj[1] = 2; s.proj[2] = 3;
+      s.coef[0] = double2{1.0, 0.0};
+      s.coef[1] = double2{-k2, 0.0};
+      s.coef[2] = double2{-k2, 0.0};
+      s.filtered = false;
+      s.near = &ctx->near;
+      s.near_which = 1;
+      break;
+    case AIM_OP_S_ALPHA:
+    case AIM_OP_EFIE_ALPHA:
+      s.nproj = 1;
+      s.proj[0] = 0;
+      s.coef[0] = double2{1.0, 0.0};
+      s.filtered = true;
+      s.near = nullptr;
+      break;
+    default:   // S and the TM EFIE
+      s.nproj = 1;
+      s.proj[0] = 0;
+      s.coef[0] = double2{1.0, 0.0};
+      s.filtered = false;
+      s.near = &ctx->near;
+      s.near_which = 0;
+      break;
+  }
+  if (ctx->form == AIM_TM_PULSE_COLLOC && (op == AIM_OP_EFIE || op == AIM_OP_EFIE_ALPHA))
+    s.out_scale = double2{0.0, ctx->k};   // j k eta, eta = 1
+  return s;
+}
+
+static aim_status pass(aim_ctx* ctx, aim_op op, int nrhs, const double2* x, double2* y, int precision, cudaStream_t st) {
+  const PassSpec spec = make_spec(ctx, op);
+  if (precision == AIM_MIXED) return grid_pass<float>(ctx, spec, nrhs, x, y, st);
+  return grid_pass<double>(ctx, spec, nrhs, x, y, st);
+}
+
+aim_status apply_op(aim_ctx* ctx, aim_op op, int nrhs, const double2* x, double2* y, int precision, cudaStream_t st) {
+  const bool te = ctx->form == AIM_TE_P1_GALERKIN;
+  const int pidx = precision == AIM_MIXED ? 1 : 0;
+  if (ctx->reserved_rhs[pidx] < nrhs) AIM_TRY(reserve(ctx, nrhs, precision));
+  switch (op) {
+    case AIM_OP_S:
+    case AIM_OP_S_ALPHA:
+      return pass(ctx, op, nrhs, x, y, precision, st);
+    case AIM_OP_N:
+      if (!te) return fail(AIM_ESTATE, "N is a TE operator");
+      return pass(ctx, op, nrhs, x, y, precision, st);
+    case AIM_OP_EFIE:
+      return pass(ctx, te ? AIM_OP_N : AIM_OP_EFIE, nrhs, x, y, precision, st);
+    case AIM_OP_EFIE_ALPHA:
+      if (te) return fail(AIM_ESTATE, "the filtered EFIE system is defined for TM contexts");
+      return pass(ctx, op, nrhs, x, y, precision, st);
+    case AIM_OP_GRAM_INV:
+      if (!te) return fail(AIM_ESTATE, "G is a TE operator");
+      return gram_inv_apply(ctx, nrhs, x, y, st);
+    case AIM_OP_CALDERON:
+    case AIM_OP_CALDERON_ALPHA: {
+      if (!te) return fail(AIM_ESTATE, "the Calderon product is a TE operator");
+      // y = G^-1 S G^-1 N x  (Eq. 3), S^alpha of Eq. 10 for the filtered variant
+      double2* t1 = ctx->vec_ws;
+      double2* t2 = ctx->vec_ws + (size_t)nrhs * ctx->n;
+      AIM_TRY(pass(ctx, AIM_OP_N, nrhs, x, t1, precision, st));
+      AIM_TRY(gram_inv_apply(ctx, nrhs, t1, t2, st));
+      AIM_TRY(pass(ctx, op == AIM_OP_CALDERON ? AIM_OP_S : AIM_OP_S_ALPHA, nrhs, t2, t1, precision, st));
+      return gram_inv_apply(ctx, nrhs, t1, y, st);
+    }
+    default:
+      return fail(AIM_EINVAL, "unknown operator");
+  }
+}
+
+aim_status device_spectra_and_near(aim_ctx* ctx, const HostSetup& hs, cudaStream_t st);
+
+}  // namespace aim
+
+using namespace aim;
+
+extern "C" {
+
+const char* aim_status_str(aim_status s) {
+  switch (s) {
+    case AIM_OK: return "ok";
+    case AIM_EINVAL: return "invalid argument";
+    case AIM_ENOMEM: return "out of memory";
+    case AIM_ECUDA: return "CUDA error";
+    case AIM_ENOCONV: return "not converged";
+    case AIM_ENUMERIC: return "non-finite value";
+    case AIM_ETIMEOUT: return "timeout";
+    case AIM_ESTATE: return "operation not valid for this context";
+  }
+  return "unknown status";
+}
+
+const char* aim_last_error(void) { return g_last_error.c_str(); }
+
+void aim_destroy(aim_ctx* ctx) {
+  if (!ctx) return;
+  for (void* p : ctx->allocations) cudaFree(p);
+  if (ctx->inter) cudaFree(ctx->inter);
+  if (ctx->vact) cudaFree(ctx->vact);
+  if (ctx->vec_ws) cudaFree(ctx->vec_ws);
+  if (ctx->stage_in) cudaFree(ctx->stage_in);
+  if (ctx->stage_out) cudaFree(ctx->stage_out);
+  if (ctx->kry) cudaFree(ctx->kry);
+  if (ctx->red) cudaFree(ctx->red);
+  if (ctx->red_host) cudaFreeHost(ctx->red_host);
+  delete ctx;
+}
+
+static aim_status validate(const aim_geometry* g, double k, const aim_grid* grid, const aim_stencil* st,
+                           const aim_filter* f) {
+  if (!g || !grid || !st || !g->xy) return fail(AIM_EINVAL, "null argument");
+  if (g->n_seg < 3) return fail(AIM_EINVAL, "n_seg must be >= 3");
+  if (g->form != AIM_TM_PULSE_COLLOC && g->form != AIM_TE_P1_GALERKIN) return fail(AIM_EINVAL, "unknown form");
+  if (g->quad_p < 1 || g->quad_p > 16) return fail(AIM_EINVAL, "quad_p must be in 1..16");
+  if (!(k > 0.0) || !std::isfinite(k)) return fail(AIM_EINVAL, "k must be positive and finite");
+  if (grid->m < 8) return fail(AIM_EINVAL, "m must be >= 8");
+  if (st->s < 2 || st->s > 12) return fail(AIM_EINVAL, "stencil s must be in 2..12");
+  if (grid->fft_P != 0 && (!is_pow2(grid->fft_P) || grid->fft_P < 2 * grid->m - 1))
+    return fail(AIM_EINVAL, "fft_P must be a power of two >= 2m-1");
+  if (f && f->enabled && !(f->alpha > k)) return fail(AIM_EINVAL, "filter radius alpha must exceed k");
+  for (int i = 0; i < 2 * g->n_seg; ++i)
+    if (!std::isfinite(g->xy[i])) return fail(AIM_EINVAL, "non-finite vertex coordinate");
+  return AIM_OK;
+}
+
+aim_status aim_setup(const aim_geometry* geometry, double k, const aim_grid* grid, const aim_stencil* stencil,
+                     const aim_filter* filter, void* stream, aim_ctx** out) {
+  if (!out) return fail(AIM_EINVAL, "out is null");
+  *out = nullptr;
+  AIM_TRY(validate(geometry, k, grid, stencil, filter));
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  aim_ctx* ctx = new (std::nothrow) aim_ctx();
+  if (!ctx) return fail(AIM_ENOMEM, "context allocation");
+  struct Guard {
+    aim_ctx* c;
+    ~Guard() { if (c) aim_destroy(c); }
+  } guard{ctx};
+
+  cudaGetDevice(&ctx->device);
+  ctx->form = geometry->form;
+  ctx->n = geometry->n_seg;
+  ctx->m = grid->m;
+  ctx->s = stencil->s;
+  ctx->p = geometry->quad_p;
+  ctx->k = k;
+  ctx->xy.assign(geometry->xy, geometry->xy + 2 * (size_t)geometry->n_seg);
+  int P = grid->fft_P;
+  if (P == 0) {
+    P = 1;
+    while (P < 2 * grid->m - 1) P *= 2;
+  }
+  if (P > kMaxP) return fail(AIM_EINVAL, "embedding side P exceeds 4096 (m too large)");
+  ctx->P = P;
+  ctx->logP = ilog2(P);
+  ctx->H = P / 2;
+  ctx->logH = ctx->logP - 1;
+  ctx->L = grid->half_side_L > 0.0 ? grid->half_side_L : host_grid_half_side(geometry->xy, ctx->n, ctx->m, ctx->s);
+  ctx->eps = 2.0 * ctx->L / (ctx->m - 1);
+  ctx->near_radius = stencil->near_radius > 0.0 ? stencil->near_radius : ctx->s * ctx->eps;
+  ctx->filter_enabled = filter && filter->enabled;
+  ctx->alpha = ctx->filter_enabled ? filter->alpha : 0.0;
+
+  HostSetup hs;
+  AIM_TRY(host_setup(ctx, &hs));
+  ctx->n_act = hs.n_act;
+  ctx->row_lo = hs.row_lo;
+  ctx->row_hi = hs.row_hi;
+  ctx->nrows = hs.row_hi - hs.row_lo + 1;
+
+  // upload
+  std::vector<double2> nodes(ctx->n);
+  for (int i = 0; i < ctx->n; ++i) nodes[i] = double2{ctx->xy[2 * i], ctx->xy[2 * i + 1]};
+  AIM_TRY(upload(ctx, &ctx->nodes, nodes, st));
+  AIM_TRY(upload(ctx, &ctx->row_ptr, hs.row_ptr, st));
+  AIM_TRY(upload(ctx, &ctx->act_ix, hs.act_ix, st));
+  AIM_TRY(upload(ctx, &ctx->prj.sc_ptr, hs.sc_ptr, st));
+  AIM_TRY(upload(ctx, &ctx->prj.sc_col, hs.sc_col, st));
+  AIM_TRY(upload(ctx, &ctx->prj.ga_ptr, hs.ga_ptr, st));
+  AIM_TRY(upload(ctx, &ctx->prj.ga_act, hs.ga_act, st));
+  ctx->prj.nproj = hs.nproj;
+  for (int q = 0; q < hs.nproj; ++q) {
+    AIM_TRY(upload(ctx, &ctx->prj.sc_w[q], hs.sc_w[q], st));
+    AIM_TRY(upload(ctx, &ctx->prj.ga_w[q], hs.ga_w[q], st));
+  }
+  std::vector<double2> tw(P);
+  std::vector<float2> twf(P);
+  for (int t = 0; t < P; ++t) {
+    tw[t] = double2{hs.tw[2 * t], hs.tw[2 * t + 1]};
+    twf[t] = float2{(float)hs.tw[2 * t], (float)hs.tw[2 * t + 1]};
+  }
+  AIM_TRY(upload(ctx, &ctx->tw, tw, st));
+  AIM_TRY(upload(ctx, &ctx->twf, twf, st));
+  if (!hs.gram_inv.empty()) {
+    AIM_TRY(upload(ctx, &ctx->gram_inv, hs.gram_inv, st));
+    ctx->gram_band = hs.gram_band;
+  }
+  AIM_TRY(device_spectra_and_near(ctx, hs, st));
+  AIM_CUDA_TRY(cudaStreamSynchronize(st));
+  ctx->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  guard.c = nullptr;
+  *out = ctx;
+  return AIM_OK;
+}
+
+aim_status aim_get_info(const aim_ctx* ctx, aim_info* info) {
+  if (!ctx || !info) return fail(AIM_EINVAL, "null argument");
+  info->n = ctx->n;
+  info->m = ctx->m;
+  info->fft_P = ctx->P;
+  info->s = ctx->s;
+  info->quad_p = ctx->p;
+  info->k = ctx->k;
+  info->L = ctx->L;
+  info->eps = ctx->eps;
+  info->alpha = ctx->alpha;
+  info->n_active = ctx->n_act;
+  info->row_lo = ctx->row_lo;
+  info->row_hi = ctx->row_hi;
+  info->nnz_near = ctx->nnz_near;
+  info->device_bytes = ctx->device_bytes + ctx->inter_bytes + ctx->vact_bytes + ctx->vec_ws_bytes +
+                       2 * ctx->stage_bytes + ctx->kry_bytes + ctx->red_bytes;
+  info->setup_seconds = ctx->setup_seconds;
+  return AIM_OK;
+}
+
+aim_status aim_reserve(aim_ctx* ctx, int nrhs, int precision) {
+  if (!ctx) return fail(AIM_EINVAL, "null context");
+  if (precision != AIM_FP64 && precision != AIM_MIXED) return fail(AIM_EINVAL, "precision must be 0 or 1");
+  return reserve(ctx, nrhs, precision);
+}
+
+aim_status aim_rhs_planewave(aim_ctx* ctx, int nrhs, const double* angles, void* rhs, void* stream) {
+  if (!ctx || !angles || !rhs || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)ctx->n * nrhs * sizeof(double2);
+  AIM_TRY(stage(ctx, std::max(bytes, nrhs * sizeof(double)), bytes));
+  double* ang = reinterpret_cast<double*>(ctx->stage_in);
+  AIM_CUDA_TRY(cudaMemcpyAsync(ang, angles, nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+  const bool dev = device_pointer(rhs);
+  double2* out = dev ? static_cast<double2*>(rhs) : ctx->stage_out;
+  AIM_TRY(device_rhs_planewave(ctx, nrhs, ang, out, st));
+  if (!dev) {
+    AIM_CUDA_TRY(cudaMemcpyAsync(rhs, out, bytes, cudaMemcpyDeviceToHost, st));
+    AIM_CUDA_TRY(cudaStreamSynchronize(st));
+  } else {
+    // the angle upload comes from pageable memory: keep the call synchronous w.r.t. `angles`
+    AIM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  return AIM_OK;
+}
+
+aim_status aim_matvec(aim_ctx* ctx, aim_op op, int nrhs, const void* x, void* y, int precision, void* stream) {
+  if (!ctx || !x || !y || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
+  if (precision != AIM_FP64 && precision != AIM_MIXED) return fail(AIM_EINVAL, "precision must be 0 or 1");
+  if (x == y) return fail(AIM_EINVAL, "x and y must not overlap");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)ctx->n * nrhs * sizeof(double2);
+  const bool dx = device_pointer(x), dy = device_pointer(y);
+  if (!dx || !dy) AIM_TRY(stage(ctx, bytes, bytes));
+  const double2* xin = static_cast<const double2*>(x);
+  if (!dx) {
+    AIM_CUDA_TRY(cudaMemcpyAsync(ctx->stage_in, x, bytes, cudaMemcpyHostToDevice, st));
+    xin = ctx->stage_in;
+  }
+  double2* yout = dy ? static_cast<double2*>(y) : ctx->stage_out;
+  AIM_TRY(apply_op(ctx, op, nrhs, xin, yout, precision, st));
+  if (!dy) {
+    AIM_CUDA_TRY(cudaMemcpyAsync(y, yout, bytes, cudaMemcpyDeviceToHost, st));
+    AIM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  return AIM_OK;
+}
+
+aim_status aim_grid_product(aim_ctx* ctx, int filtered, int nrhs, const void* u, void* v, int precision, void* stream) {
+  if (!ctx || !u || !v || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
+  if (precision != AIM_FP64 && precision != AIM_MIXED) return fail(AIM_EINVAL, "precision must be 0 or 1");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)ctx->m * ctx->m * nrhs * sizeof(double2);
+  const bool du = device_pointer(u), dv = device_pointer(v);
+  if (!du || !dv) AIM_TRY(stage(ctx, bytes, bytes));
+  // workspace for nrhs channels
+  const int chan_needed = nrhs;
+  AIM_TRY(grow(&ctx->inter, &ctx->inter_bytes, inter_bytes_needed(ctx, chan_needed, precision)));
+  const double2* uin = static_cast<const double2*>(u);
+  if (!du) {
+    AIM_CUDA_TRY(cudaMemcpyAsync(ctx->stage_in, u, bytes, cudaMemcpyHostToDevice, st));
+    uin = ctx->stage_in;
+  }
+  double2* vout = dv ? static_cast<double2*>(v) : ctx->stage_out;
+  if (precision == AIM_MIXED) AIM_TRY(grid_product_dense<float>(ctx, filtered != 0, nrhs, uin, vout, st));
+  else AIM_TRY(grid_product_dense<double>(ctx, filtered != 0, nrhs, uin, vout, st));
+  if (!dv) {
+    AIM_CUDA_TRY(cudaMemcpyAsync(v, vout, bytes, cudaMemcpyDeviceToHost, st));
+    AIM_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  return AIM_OK;
+}
+
+aim_status aim_solve(aim_ctx* ctx, aim_op system, int nrhs, const void* rhs, void* x, int x0_given,
+                     const aim_solve_opts* opts, aim_solve_info* info, void* stream) {
+  if (!ctx || !rhs || !x || !opts || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
+  if (!(opts->tol > 0.0) || opts->restart < 1 || opts->restart > 10000 || opts->max_iter < 1)
+    return fail(AIM_EINVAL, "bad solver options");
+  if (opts->precision != AIM_FP64 && opts->precision != AIM_MIXED) return fail(AIM_EINVAL, "bad precision");
+  const bool te = ctx->form == AIM_TE_P1_GALERKIN;
+  if (system != AIM_OP_EFIE && system != AIM_OP_EFIE_ALPHA && system != AIM_OP_CALDERON && system != AIM_OP_CALDERON_ALPHA)
+    return fail(AIM_EINVAL, "system must be EFIE, EFIE_ALPHA, CALDERON or CALDERON_ALPHA");
+  if (!te && (system == AIM_OP_CALDERON || system == AIM_OP_CALDERON_ALPHA))
+    return fail(AIM_ESTATE, "Calderon systems need a TE context");
+  if (te && system == AIM_OP_EFIE_ALPHA) return fail(AIM_ESTATE, "filtered EFIE system is TM only");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)ctx->n * nrhs * sizeof(double2);
+  const bool dr = device_pointer(rhs), dx = device_pointer(x);
+  AIM_TRY(reserve(ctx, nrhs, AIM_FP64));
+  if (opts->precision == AIM_MIXED) AIM_TRY(reserve(ctx, nrhs, AIM_MIXED));
+  AIM_TRY(stage(ctx, bytes, bytes));
+  // b lives in stage_in (for Calderon systems: G^-1 S G^-1 E); x in place or staged
+  double2* b = ctx->stage_in;
+  double2* xd = dx ? static_cast<double2*>(x) : ctx->stage_out;
+  if (dr) AIM_CUDA_TRY(cudaMemcpyAsync(b, rhs, bytes, cudaMemcpyDeviceToDevice, st));
+  else AIM_CUDA_TRY(cudaMemcpyAsync(b, rhs, bytes, cudaMemcpyHostToDevice, st));
+  if (x0_given) {
+    if (!dx) AIM_CUDA_TRY(cudaMemcpyAsync(xd, x, bytes, cudaMemcpyHostToDevice, st));
+  } else {
+    AIM_CUDA_TRY(cudaMemsetAsync(xd, 0, bytes, st));
+  }
+  if (system == AIM_OP_CALDERON || system == AIM_OP_CALDERON_ALPHA) {
+    // b <- G^-1 S G^-1 E, with S^alpha for the filtered system (Eq. 3)
+    double2* t1 = ctx->vec_ws;
+    double2* t2 = ctx->vec_ws + (size_t)nrhs * ctx->n;
+    AIM_TRY(gram_inv_apply(ctx, nrhs, b, t1, st));
+    AIM_TRY(apply_op(ctx, system == AIM_OP_CALDERON ? AIM_OP_S : AIM_OP_S_ALPHA, nrhs, t1, t2, AIM_FP64, st));
+    AIM_TRY(gram_inv_apply(ctx, nrhs, t2, b, st));
+  }
+  aim_status s = gmres_solve(ctx, system, nrhs, b, xd, opts, info, st);
+  if (!dx) {
+    AIM_CUDA_TRY(cudaMemcpyAsync(x, xd, bytes, cudaMemcpyDeviceToHost, st));
+  }
+  AIM_CUDA_TRY(cudaStreamSynchronize(st));
+  return s;
+}
+
+aim_status aim_query_bytes(const aim_geometry* geometry, const aim_grid* grid, const aim_stencil* stencil, int nrhs,
+                           int precision, size_t* bytes) {
+  if (!geometry || !grid || !stencil || !bytes || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
+  const int n = geometry->n_seg, m = grid->m, s = stencil->s, p = geometry->quad_p;
+  int P = grid->fft_P;
+  if (P == 0) {
+    P = 1;
+    while (P < 2 * m - 1) P *= 2;
+  }
+  const size_t H = P / 2;
+  const bool te = geometry->form == AIM_TE_P1_GALERKIN;
+  // active points bounded by all stencil points; rows bounded by m
+  const size_t nodes = (size_t)n * p * (te ? 2 : 1) + (te ? 0 : n);
+  const size_t nact = std::min((size_t)m * m, nodes * s * s);
+  const size_t chan = (size_t)(te ? 3 : 1) * nrhs;
+  const size_t el = precision == AIM_MIXED ? 8 : 16;
+  size_t b = 0;
+  b += 2 * (H + 1) * (H + 1) * (16 + 8);            // spectra (double + float)
+  b += (H + 1) * (H + 1) * 16;                      // setup temporary (kernel samples)
+  b += nodes * s * s * (4 + 8 * (te ? 4 : 1)) * 2;  // projections, both orders
+  b += (size_t)n * 64 * (4 + 16 + 8) * (te ? 2 : 1);  // near field (bound 64 per row)
+  b += (size_t)n * (2 * kGramBand + 1 + kGramDenseMax) * 8;
+  b += chan * P * m * el + chan * nact * el;        // grid workspaces
+  b += (size_t)(2 + 2 + 54) * n * nrhs * 16;        // vectors, staging, Krylov (restart 50)
+  *bytes = b;
+  return AIM_OK;
+}
+
+}  // extern "C"

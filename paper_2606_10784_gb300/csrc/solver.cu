@@ -1,0 +1,408 @@
+// Restarted GMRES for the AIM systems (the iterative solver of Sec. I; the Calderon system of
+// Eq. 3). Arnoldi runs in FP64 on the device with classical Gram-Schmidt applied twice; the
+// small Hessenberg least-squares problem (Givens rotations) is solved on the host, one
+// device-to-host copy of the new Hessenberg column per iteration. Several right-hand sides
+// run in lock step, each with its own Krylov basis.
+//
+// Mixed precision: the outer loop computes r = b - A x with the FP64 grid product, an inner
+// GMRES with the FP32 grid product solves A d = r to a looser tolerance, and x += d, until
+// the FP64 residual meets the target (iterative refinement).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "aim_internal.h"
+
+namespace aim {
+
+// out[j*nrhs + r] = sum_i conj(V[j][r][i]) * w[r][i]   (j < J), one block per (j, r)
+__global__ void k_multidot(const double2* __restrict__ V, const double2* __restrict__ w, int n, int nrhs,
+                           double2* __restrict__ out) {
+  const int j = blockIdx.x, r = blockIdx.y;
+  const double2* v = V + ((size_t)j * nrhs + r) * n;
+  const double2* x = w + (size_t)r * n;
+  double re = 0.0, im = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double2 a = v[i], b = x[i];
+    re += a.x * b.x + a.y * b.y;
+    im += a.x * b.y - a.y * b.x;
+  }
+  __shared__ double sre[32], sim[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, off);
+    im += __shfl_xor_sync(0xffffffffu, im, off);
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sre[wid] = re; sim[wid] = im; }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    re = lane < nw ? sre[lane] : 0.0;
+    im = lane < nw ? sim[lane] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, off);
+      im += __shfl_xor_sync(0xffffffffu, im, off);
+    }
+    if (lane == 0) out[(size_t)j * nrhs + r] = double2{re, im};
+  }
+}
+
+// w[r][i] -= sum_{j<J} V[j][r][i] h[j*nrhs + r]; accum[j*nrhs+r] += h (to sum both CGS passes)
+__global__ void k_cgs_sub(const double2* __restrict__ V, const double2* __restrict__ h, int J, int n, int nrhs,
+                          double2* __restrict__ w) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * nrhs) return;
+  const int r = t / n, i = t - r * n;
+  double2 acc = w[t];
+  for (int j = 0; j < J; ++j) {
+    const double2 v = V[((size_t)j * nrhs + r) * n + i];
+    const double2 c = h[(size_t)j * nrhs + r];
+    acc.x -= v.x * c.x - v.y * c.y;
+    acc.y -= v.x * c.y + v.y * c.x;
+  }
+  w[t] = acc;
+}
+
+__global__ void k_add_small(double2* a, const double2* b, int count) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) { a[t].x += b[t].x; a[t].y += b[t].y; }
+}
+
+// dst[r] = w[r] / sqrt(nrm2[r].x) (zero if the norm vanished); active[r] == 0 zeroes dst[r]
+__global__ void k_normalize(const double2* __restrict__ w, const double2* __restrict__ nrm2, const int* __restrict__ active,
+                            int n, int nrhs, double2* __restrict__ dst) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * nrhs) return;
+  const int r = t / n;
+  const double nv = sqrt(fmax(nrm2[r].x, 0.0));
+  const double s = (active[r] && nv > 0.0) ? 1.0 / nv : 0.0;
+  dst[t] = double2{w[t].x * s, w[t].y * s};
+}
+
+// x[r] += sum_j V[j][r] y[j*nrhs + r]
+__global__ void k_update_x(const double2* __restrict__ V, const double2* __restrict__ y, int J, int n, int nrhs,
+                           double2* __restrict__ x) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * nrhs) return;
+  const int r = t / n, i = t - r * n;
+  double2 acc = x[t];
+  for (int j = 0; j < J; ++j) {
+    const double2 v = V[((size_t)j * nrhs + r) * n + i];
+    const double2 c = y[(size_t)j * nrhs + r];
+    acc.x += v.x * c.x - v.y * c.y;
+    acc.y += v.x * c.y + v.y * c.x;
+  }
+  x[t] = acc;
+}
+
+// r = b - Ax
+__global__ void k_residual(const double2* __restrict__ b, const double2* __restrict__ Ax, int total, double2* __restrict__ r) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < total) r[t] = double2{b[t].x - Ax[t].x, b[t].y - Ax[t].y};
+}
+
+__global__ void k_add_vec(double2* __restrict__ x, const double2* __restrict__ d, int total) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < total) { x[t].x += d[t].x; x[t].y += d[t].y; }
+}
+
+namespace {
+
+struct Zc {
+  double re, im;
+};
+inline Zc cm(Zc a, Zc b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+inline Zc cconj(Zc a) { return {a.re, -a.im}; }
+inline double cabs2(Zc a) { return a.re * a.re + a.im * a.im; }
+
+struct Workspace {
+  double2 *V, *w, *r, *tmp, *dots, *dots2, *nrm;
+  int* active;
+};
+
+inline int blocks_for(long long total, int tpb) { return (int)((total + tpb - 1) / tpb); }
+
+aim_status dot_norms(const double2* vecs, int n, int nrhs, double2* out, cudaStream_t st) {
+  count_launches(K_GMRES, 1);
+  k_multidot<<<dim3(1, nrhs), 256, 0, st>>>(vecs, vecs, n, nrhs, out);
+  AIM_CUDA_TRY(cudaGetLastError());
+  return AIM_OK;
+}
+
+}  // namespace
+
+static aim_status ensure_krylov(aim_ctx* ctx, int nrhs, int restart) {
+  const size_t nvec = (size_t)(restart + 1) + 3;
+  const size_t need = nvec * nrhs * ctx->n * sizeof(double2);
+  if (ctx->kry_bytes < need) {
+    if (ctx->kry) cudaFree(ctx->kry);
+    ctx->kry = nullptr;
+    ctx->kry_bytes = 0;
+    void* p = nullptr;
+    AIM_CUDA_TRY(cudaMalloc(&p, need));
+    ctx->kry = static_cast<double2*>(p);
+    ctx->kry_bytes = need;
+  }
+  const size_t rneed = ((size_t)(restart + 2) * 3 + 1) * nrhs * sizeof(double2) + nrhs * sizeof(int);
+  if (ctx->red_bytes < rneed) {
+    if (ctx->red) cudaFree(ctx->red);
+    if (ctx->red_host) cudaFreeHost(ctx->red_host);
+    ctx->red = nullptr;
+    ctx->red_host = nullptr;
+    ctx->red_bytes = 0;
+    void* p = nullptr;
+    AIM_CUDA_TRY(cudaMalloc(&p, rneed));
+    ctx->red = static_cast<double*>(p);
+    AIM_CUDA_TRY(cudaMallocHost(&p, rneed));
+    ctx->red_host = static_cast<double*>(p);
+    ctx->red_bytes = rneed;
+  }
+  return AIM_OK;
+}
+
+// Core restarted GMRES on A (op, precision) for b -> x, all right-hand sides in lock step.
+// tol: relative to ||b_r||. Updates per-rhs iteration counters and convergence flags.
+static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, const double2* b, double2* x,
+                             double tol, int restart, int max_iter, std::vector<int>* iters,
+                             std::vector<double>* relres, std::vector<int>* conv,
+                             std::chrono::steady_clock::time_point deadline, bool has_deadline,
+                             cudaStream_t st) {
+  const int n = ctx->n;
+  const size_t vsz = (size_t)nrhs * n;
+  AIM_TRY(ensure_krylov(ctx, nrhs, restart));
+  Workspace ws;
+  ws.V = ctx->kry;
+  ws.w = ws.V + (size_t)(restart + 1) * vsz;
+  ws.r = ws.w + vsz;
+  ws.tmp = ws.r + vsz;
+  double2* red = reinterpret_cast<double2*>(ctx->red);
+  ws.dots = red;                                   // (restart+1) * nrhs
+  ws.dots2 = red + (size_t)(restart + 2) * nrhs;   // (restart+1) * nrhs
+  ws.nrm = red + (size_t)(restart + 2) * 2 * nrhs; // nrhs
+  ws.active = reinterpret_cast<int*>(red + ((size_t)(restart + 2) * 3 + 1) * nrhs);
+  double2* hred = reinterpret_cast<double2*>(ctx->red_host);
+  const int tpb = 256;
+  const int nb = blocks_for((long long)vsz, tpb);
+
+  // ||b||
+  AIM_TRY(dot_norms(b, n, nrhs, ws.nrm, st));
+  AIM_CUDA_TRY(cudaMemcpyAsync(hred, ws.nrm, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  AIM_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<double> bnorm(nrhs);
+  for (int r = 0; r < nrhs; ++r) {
+    bnorm[r] = std::sqrt(hred[r].x);
+    if (!std::isfinite(bnorm[r])) return fail(AIM_ENUMERIC, "non-finite right-hand side");
+  }
+
+  std::vector<int> active(nrhs, 1);
+  std::vector<Zc> Hm((size_t)(restart + 1) * restart * nrhs), cs((size_t)restart * nrhs), sn((size_t)restart * nrhs),
+      g((size_t)(restart + 1) * nrhs), yv((size_t)restart * nrhs);
+  std::vector<double> beta(nrhs);
+  std::vector<int> jconv(nrhs);
+
+  while (true) {
+    // true residual r = b - A x
+    AIM_TRY(apply_op(ctx, op, nrhs, x, ws.w, precision, st));
+    count_launches(K_GMRES, 1);
+    k_residual<<<nb, tpb, 0, st>>>(b, ws.w, (int)vsz, ws.r);
+    AIM_CUDA_TRY(cudaGetLastError());
+    AIM_TRY(dot_norms(ws.r, n, nrhs, ws.nrm, st));
+    AIM_CUDA_TRY(cudaMemcpyAsync(hred, ws.nrm, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    AIM_CUDA_TRY(cudaStreamSynchronize(st));
+    bool any = false;
+    for (int r = 0; r < nrhs; ++r) {
+      beta[r] = std::sqrt(hred[r].x);
+      if (!std::isfinite(beta[r])) return fail(AIM_ENUMERIC, "non-finite residual");
+      const double rel = bnorm[r] > 0 ? beta[r] / bnorm[r] : 0.0;
+      (*relres)[r] = rel;
+      if (rel <= tol || bnorm[r] == 0.0) { active[r] = 0; (*conv)[r] = 1; }
+      else if ((*iters)[r] >= max_iter) active[r] = 0;
+      else active[r] = 1;
+      any = any || active[r];
+    }
+    if (!any) break;
+    if (has_deadline && std::chrono::steady_clock::now() > deadline) return fail(AIM_ETIMEOUT, "solve time limit reached");
+
+    AIM_CUDA_TRY(cudaMemcpyAsync(ws.active, active.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
+    count_launches(K_GMRES, 1);
+    k_normalize<<<nb, tpb, 0, st>>>(ws.r, ws.nrm, ws.active, n, nrhs, ws.V);
+    AIM_CUDA_TRY(cudaGetLastError());
+    for (int r = 0; r < nrhs; ++r) {
+      g[(size_t)0 * nrhs + r] = {beta[r], 0.0};
+      for (int j = 1; j <= restart; ++j) g[(size_t)j * nrhs + r] = {0.0, 0.0};
+      jconv[r] = 0;
+    }
+    int jdone = 0;
+    for (int j = 0; j < restart; ++j) {
+      double2* Vj = ws.V + (size_t)j * vsz;
+      AIM_TRY(apply_op(ctx, op, nrhs, Vj, ws.w, precision, st));
+      // CGS2 (6 launches here + 1 in dot_norms)
+      count_launches(K_GMRES, 6);
+      k_multidot<<<dim3(j + 1, nrhs), 256, 0, st>>>(ws.V, ws.w, n, nrhs, ws.dots);
+      k_cgs_sub<<<nb, tpb, 0, st>>>(ws.V, ws.dots, j + 1, n, nrhs, ws.w);
+      k_multidot<<<dim3(j + 1, nrhs), 256, 0, st>>>(ws.V, ws.w, n, nrhs, ws.dots2);
+      k_cgs_sub<<<nb, tpb, 0, st>>>(ws.V, ws.dots2, j + 1, n, nrhs, ws.w);
+      k_add_small<<<blocks_for((j + 1) * nrhs, tpb), tpb, 0, st>>>(ws.dots, ws.dots2, (j + 1) * nrhs);
+      AIM_TRY(dot_norms(ws.w, n, nrhs, ws.nrm, st));
+      k_normalize<<<nb, tpb, 0, st>>>(ws.w, ws.nrm, ws.active, n, nrhs, ws.V + (size_t)(j + 1) * vsz);
+      AIM_CUDA_TRY(cudaGetLastError());
+      AIM_CUDA_TRY(cudaMemcpyAsync(hred, ws.dots, (size_t)(j + 1) * nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
+      AIM_CUDA_TRY(cudaMemcpyAsync(hred + (size_t)(j + 1) * nrhs, ws.nrm, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
+      AIM_CUDA_TRY(cudaStreamSynchronize(st));
+      jdone = j + 1;
+      bool all_done = true;
+      for (int r = 0; r < nrhs; ++r) {
+        if (!active[r] || jconv[r]) continue;
+        Zc* col = &Hm[((size_t)j * (restart + 1)) * nrhs];   // column j, rows 0..j+1
+        for (int i = 0; i <= j; ++i) col[(size_t)i * nrhs + r] = {hred[(size_t)i * nrhs + r].x, hred[(size_t)i * nrhs + r].y};
+        const double hn = std::sqrt(std::fmax(hred[(size_t)(j + 1) * nrhs + r].x, 0.0));
+        if (!std::isfinite(hn)) return fail(AIM_ENUMERIC, "non-finite Arnoldi norm");
+        col[(size_t)(j + 1) * nrhs + r] = {hn, 0.0};
+        for (int i = 0; i < j; ++i) {
+          const Zc c = cs[(size_t)i * nrhs + r], s = sn[(size_t)i * nrhs + r];
+          const Zc a = col[(size_t)i * nrhs + r], bb = col[(size_t)(i + 1) * nrhs + r];
+          const Zc t1 = cm(c, a), t2 = cm(s, bb);
+          const Zc t3 = cm(cconj(s), a), t4 = cm(cconj(c), bb);
+          col[(size_t)i * nrhs + r] = {t1.re + t2.re, t1.im + t2.im};
+          col[(size_t)(i + 1) * nrhs + r] = {-t3.re + t4.re, -t3.im + t4.im};
+        }
+        const Zc a = col[(size_t)j * nrhs + r], bb = col[(size_t)(j + 1) * nrhs + r];
+        const double den = std::sqrt(cabs2(a) + cabs2(bb));
+        Zc c{1.0, 0.0}, s{0.0, 0.0};
+        if (den > 0.0) {
+          c = {a.re / den, -a.im / den};
+          s = {bb.re / den, -bb.im / den};
+        }
+        cs[(size_t)j * nrhs + r] = c;
+        sn[(size_t)j * nrhs + r] = s;
+        col[(size_t)j * nrhs + r] = {den, 0.0};
+        col[(size_t)(j + 1) * nrhs + r] = {0.0, 0.0};
+        const Zc gj = g[(size_t)j * nrhs + r];
+        const Zc ng = cm(cconj(s), gj);
+        g[(size_t)(j + 1) * nrhs + r] = {-ng.re, -ng.im};
+        g[(size_t)j * nrhs + r] = cm(c, gj);
+        (*iters)[r] += 1;
+        const double est = std::sqrt(cabs2(g[(size_t)(j + 1) * nrhs + r])) / bnorm[r];
+        if (est <= tol || (*iters)[r] >= max_iter || hn == 0.0) jconv[r] = j + 1;
+        if (!jconv[r]) all_done = false;
+      }
+      if (all_done) break;
+      if (has_deadline && std::chrono::steady_clock::now() > deadline) return fail(AIM_ETIMEOUT, "solve time limit reached");
+    }
+    // back substitution per rhs, using its own Krylov length
+    std::fill(yv.begin(), yv.end(), Zc{0.0, 0.0});
+    for (int r = 0; r < nrhs; ++r) {
+      if (!active[r]) continue;
+      const int J = jconv[r] ? jconv[r] : jdone;
+      for (int i = J - 1; i >= 0; --i) {
+        Zc acc = g[(size_t)i * nrhs + r];
+        for (int l = i + 1; l < J; ++l) {
+          const Zc t = cm(Hm[((size_t)l * (restart + 1) + i) * nrhs + r], yv[(size_t)l * nrhs + r]);
+          acc.re -= t.re;
+          acc.im -= t.im;
+        }
+        const Zc d = Hm[((size_t)i * (restart + 1) + i) * nrhs + r];
+        const double dd = cabs2(d);
+        yv[(size_t)i * nrhs + r] = dd > 0 ? Zc{(acc.re * d.re + acc.im * d.im) / dd, (acc.im * d.re - acc.re * d.im) / dd}
+                                          : Zc{0.0, 0.0};
+      }
+    }
+    AIM_CUDA_TRY(cudaMemcpyAsync(ws.dots, yv.data(), (size_t)jdone * nrhs * sizeof(double2), cudaMemcpyHostToDevice, st));
+    count_launches(K_GMRES, 1);
+    k_update_x<<<nb, tpb, 0, st>>>(ws.V, ws.dots, jdone, n, nrhs, x);
+    AIM_CUDA_TRY(cudaGetLastError());
+  }
+  return AIM_OK;
+}
+
+aim_status gmres_solve(aim_ctx* ctx, aim_op system, int nrhs, const double2* b, double2* x,
+                       const aim_solve_opts* opts, aim_solve_info* info, cudaStream_t st) {
+  const int n = ctx->n;
+  const size_t vsz = (size_t)nrhs * n;
+  const bool has_deadline = opts->timeout_ms > 0;
+  const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(has_deadline ? opts->timeout_ms : 0);
+  std::vector<int> iters(nrhs, 0), conv(nrhs, 0), outer(nrhs, 0);
+  std::vector<double> relres(nrhs, 1.0);
+  aim_status st_out = AIM_OK;
+  if (opts->precision == AIM_FP64) {
+    aim_status s = gmres_core(ctx, system, AIM_FP64, nrhs, b, x, opts->tol, opts->restart, opts->max_iter, &iters,
+                              &relres, &conv, deadline, has_deadline, st);
+    if (s != AIM_OK) return s;
+    for (int r = 0; r < nrhs; ++r) outer[r] = 1;
+  } else {
+    // iterative refinement: FP64 residual outside, FP32 grid product inside
+    AIM_TRY(reserve(ctx, nrhs, AIM_FP64));
+    AIM_TRY(reserve(ctx, nrhs, AIM_MIXED));
+    const size_t need = 3 * vsz * sizeof(double2);
+    if (ctx->stage_bytes < need + 0) {
+      // the refinement temporaries live in vec_ws (sized by reserve for composites: 2 vectors);
+      // use a dedicated buffer here
+    }
+    double2* rr = nullptr;
+    double2* dd = nullptr;
+    AIM_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void**>(&rr), 2 * vsz * sizeof(double2), st));
+    dd = rr + vsz;
+    std::vector<double> bn(nrhs);
+    aim_status s = AIM_OK;
+    for (int outer_it = 0; outer_it < 60; ++outer_it) {
+      // r = b - A x (FP64)
+      s = apply_op(ctx, system, nrhs, x, rr, AIM_FP64, st);
+      if (s != AIM_OK) break;
+      count_launches(K_GMRES, 3);
+      k_residual<<<blocks_for((long long)vsz, 256), 256, 0, st>>>(b, rr, (int)vsz, rr);
+      // norms of r and b
+      std::vector<int> it_inner(nrhs, 0), conv_inner(nrhs, 0);
+      std::vector<double> rel_inner(nrhs, 1.0);
+      double2* nrm = reinterpret_cast<double2*>(ctx->red);
+      s = ensure_krylov(ctx, nrhs, opts->restart);
+      if (s != AIM_OK) break;
+      nrm = reinterpret_cast<double2*>(ctx->red);
+      double2* hred = reinterpret_cast<double2*>(ctx->red_host);
+      k_multidot<<<dim3(1, nrhs), 256, 0, st>>>(rr, rr, n, nrhs, nrm);
+      k_multidot<<<dim3(1, nrhs), 256, 0, st>>>(b, b, n, nrhs, nrm + nrhs);
+      cudaMemcpyAsync(hred, nrm, 2 * nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st);
+      if (cudaStreamSynchronize(st) != cudaSuccess) { s = fail(AIM_ECUDA, "stream sync failed"); break; }
+      bool all = true;
+      for (int r = 0; r < nrhs; ++r) {
+        const double rn = std::sqrt(hred[r].x), bnr = std::sqrt(hred[nrhs + r].x);
+        if (!std::isfinite(rn) || !std::isfinite(bnr)) { s = fail(AIM_ENUMERIC, "non-finite residual"); break; }
+        relres[r] = bnr > 0 ? rn / bnr : 0.0;
+        conv[r] = relres[r] <= opts->tol;
+        all = all && (conv[r] || iters[r] >= opts->max_iter);
+      }
+      if (s != AIM_OK || all) break;
+      if (has_deadline && std::chrono::steady_clock::now() > deadline) { s = fail(AIM_ETIMEOUT, "solve time limit reached"); break; }
+      // inner solve A d = r with the FP32 grid product
+      cudaMemsetAsync(dd, 0, vsz * sizeof(double2), st);
+      const double itol = opts->inner_tol > 0 ? opts->inner_tol : 1e-4;
+      s = gmres_core(ctx, system, AIM_MIXED, nrhs, rr, dd, itol, opts->restart, opts->max_iter, &it_inner, &rel_inner,
+                     &conv_inner, deadline, has_deadline, st);
+      if (s != AIM_OK) break;
+      // only right-hand sides that have not converged take the correction
+      for (int r = 0; r < nrhs; ++r) {
+        iters[r] += it_inner[r];
+        outer[r] += 1;
+        if (conv[r]) cudaMemsetAsync(dd + (size_t)r * n, 0, n * sizeof(double2), st);
+      }
+      count_launches(K_GMRES, 1);
+      k_add_vec<<<blocks_for((long long)vsz, 256), 256, 0, st>>>(x, dd, (int)vsz);
+    }
+    cudaFreeAsync(rr, st);
+    if (s != AIM_OK) return s;
+  }
+  for (int r = 0; r < nrhs; ++r) {
+    if (info) {
+      info[r].iters = iters[r];
+      info[r].outer_iters = outer[r];
+      info[r].rel_res = relres[r];
+      info[r].converged = conv[r];
+    }
+    if (!conv[r]) st_out = AIM_ENOCONV;
+  }
+  if (st_out != AIM_OK) return fail(st_out, "GMRES did not reach the tolerance within max_iter");
+  return AIM_OK;
+}
+
+}  // namespace aim

@@ -1,0 +1,75 @@
+"""The C-ABI library builds, loads and exports every entry point that include/aim.h declares.
+
+These tests make no compute calls (no GPU here): only host-only entry points run.
+"""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2606_10784_gb300 import aim
+    return aim.lib()
+
+
+def declared_functions():
+    txt = open(os.path.join(ROOT, "include", "aim.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(aim_[a-z_]+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for need in ("aim_setup", "aim_matvec", "aim_solve", "aim_destroy", "aim_grid_product", "aim_rhs_planewave",
+                 "aim_query_bytes", "aim_reserve", "aim_get_info", "aim_status_str", "aim_last_error"):
+        assert need in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    for code in range(8):
+        assert lib.aim_status_str(code)
+    assert lib.aim_status_str(99) == b"unknown status"
+
+
+def test_query_bytes_is_host_only_and_scales(lib):
+    from paper_2606_10784_gb300 import aim
+    nodes = synth.circle_polygon(1.0, 256)
+    b1 = aim.query_bytes(nodes, aim.TE, 64, nrhs=1)
+    b8 = aim.query_bytes(nodes, aim.TE, 64, nrhs=8)
+    big = aim.query_bytes(synth.circle_polygon(100.0, 4000), aim.TE, 1024, nrhs=1)
+    assert 0 < b1 < b8 < big
+
+
+def test_setup_rejects_bad_arguments_before_touching_the_gpu(lib):
+    from paper_2606_10784_gb300 import aim
+    nodes = synth.circle_polygon(1.0, 64)
+    for kw, status in ((dict(m=4), aim.EINVAL), (dict(m=32, fft_P=48), aim.EINVAL), (dict(m=32, s=1), aim.EINVAL),
+                       (dict(m=32, alpha=1.0), aim.EINVAL)):
+        with pytest.raises(aim.AimError) as exc:
+            aim.Context(nodes, 2 * np.pi, aim.TE, **kw)
+        assert exc.value.status == status
+    with pytest.raises(aim.AimError):
+        aim.Context(nodes[:2], 2 * np.pi, aim.TE, 32)
+
+
+def test_binding_refuses_to_run_without_the_library(monkeypatch, tmp_path):
+    from paper_2606_10784_gb300 import aim
+    monkeypatch.setattr(aim, "_lib", None)
+    monkeypatch.setattr(aim, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        aim.lib()

@@ -1,0 +1,253 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, element by element.
+
+FP64 mode: relative L2 <= 1e-10 per vector (the path computes in complex128; the gap to the
+oracle is rounding order, quadrature rules that agree to ~1e-13, and Bessel evaluations).
+Mixed mode (complex64 grid products): relative L2 <= 1e-5 (single precision FFT of length
+P <= 4096 accumulates ~1e-6 relative error).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import aim as oaim
+from oracle import dense, solve
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+K = 2.0 * math.pi
+TOL64 = 1e-10
+TOL32 = 1e-5
+
+
+@pytest.fixture(scope="module")
+def aimlib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2606_10784_gb300 import aim
+    return aim
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b))
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to("cuda:0")
+
+
+def run_matvec(ctx, op, x, precision=0):
+    xd = dev(x)
+    yd = torch.empty_like(xd)
+    ctx.matvec(op, xd, yd, precision=precision)
+    torch.cuda.synchronize()
+    return yd.cpu().numpy()
+
+
+# --------------------------------------------------------------------------------------
+# grid product alone (Eq. 8 bracket, Eq. 10 bracket)
+# --------------------------------------------------------------------------------------
+@pytest.mark.parametrize("m,P,alpha_k,radius", [(16, 32, 3.0, 1.0), (24, 64, 4.0, 1.0), (64, 128, 8.0, 1.0),
+                                                (128, 256, 2.0, 8.0)])
+def test_grid_product_matches_oracle(aimlib, m, P, alpha_k, radius):
+    # radius 8 puts kernel samples at k r up to ~150 (the large-argument Bessel branch)
+    nodes = synth.circle_polygon(radius, 96 if radius < 2 else 400)
+    ctx = aimlib.Context(nodes, K, aimlib.TE, m, fft_P=P, alpha=alpha_k * K)
+    inf = ctx.info()
+    ref = oaim.TEOperators(nodes, K, m, P, alpha=alpha_k * K, L=inf["L"], near=False)
+    assert abs(inf["L"] - oaim.grid_half_side(nodes, m, 4)) <= 1e-15 * inf["L"]
+    u = synth.random_grid(m, 3, seed=m)
+    u[:, :inf["row_lo"], :] = 0
+    u[:, inf["row_hi"] + 1:, :] = 0
+    for filtered in (False, True):
+        want = ref.grid_product(u, filtered)
+        want[:, :inf["row_lo"], :] = 0
+        want[:, inf["row_hi"] + 1:, :] = 0
+        for prec, tol in ((0, TOL64), (1, TOL32)):
+            ud = dev(u)
+            vd = torch.empty_like(ud)
+            ctx.grid_product(ud, vd, filtered, precision=prec)
+            torch.cuda.synchronize()
+            got = vd.cpu().numpy()
+            rows = slice(inf["row_lo"], inf["row_hi"] + 1)
+            for r in range(3):
+                assert rel(got[r, rows], want[r, rows]) < tol, (filtered, prec, r)
+    ctx.close()
+
+
+# --------------------------------------------------------------------------------------
+# operators
+# --------------------------------------------------------------------------------------
+TE_CASES = [
+    ("circle_n64_m32", lambda: synth.circle_polygon(1.0, 64), 32, 64, 6.0),
+    ("star_n80_m32", lambda: synth.StarContour.from_seed(0).polygon(6.0, 80), 32, 64, 3.0),
+    ("star_n150_m48_P128", lambda: synth.StarContour.from_seed(2).polygon(12.0, 150), 48, 128, 2.5),
+    # N > 512 (banded G^-1) and kernel samples beyond k r = 25 (large-argument Bessel branch)
+    ("star_n600_m128_P256", lambda: synth.StarContour.from_seed(4).polygon(60.0, 600), 128, 256, 2.0),
+]
+
+
+@pytest.fixture(scope="module", params=TE_CASES, ids=[c[0] for c in TE_CASES])
+def te_pair(request, aimlib):
+    _, mk, m, P, ak = request.param
+    nodes = mk()
+    ctx = aimlib.Context(nodes, K, aimlib.TE, m, fft_P=P, alpha=ak * K)
+    ref = oaim.TEOperators(nodes, K, m, P, alpha=ak * K, L=ctx.info()["L"])
+    yield nodes, ctx, ref
+    ctx.close()
+
+
+@pytest.mark.parametrize("op", ["S", "S_alpha", "N", "gram_inv", "calderon", "calderon_alpha", "efie"])
+def test_te_operator_matches_oracle(te_pair, op):
+    nodes, ctx, ref = te_pair
+    n = len(nodes)
+    x = synth.random_coeffs(n, 3, seed=7)
+    f = {"S": ref.S, "S_alpha": ref.S_alpha, "N": ref.N, "gram_inv": ref.gram_solve,
+         "calderon": lambda v: ref.calderon(v, filtered=False), "calderon_alpha": lambda v: ref.calderon(v, True),
+         "efie": ref.N}[op]
+    want = np.stack([f(v) for v in x])
+    got = run_matvec(ctx, op, x)
+    for r in range(3):
+        assert rel(got[r], want[r]) < TOL64, (op, r, rel(got[r], want[r]))
+    if op != "gram_inv":
+        got32 = run_matvec(ctx, op, x, precision=1)
+        for r in range(3):
+            assert rel(got32[r], want[r]) < TOL32, (op, r, rel(got32[r], want[r]))
+
+
+def test_te_near_field_count_matches_oracle(te_pair):
+    nodes, ctx, ref = te_pair
+    assert ctx.info()["nnz_near"] == len(ref.near_rows)
+
+
+TM_CASES = [
+    ("circle_n256_m64", lambda: synth.circle_polygon(1.0, 256), 64, 128, 8.0),
+    ("star_n100_m40", lambda: synth.StarContour.from_seed(1).polygon(8.0, 100), 40, 128, 3.0),
+]
+
+
+@pytest.fixture(scope="module", params=TM_CASES, ids=[c[0] for c in TM_CASES])
+def tm_pair(request, aimlib):
+    _, mk, m, P, ak = request.param
+    nodes = mk()
+    ctx = aimlib.Context(nodes, K, aimlib.TM, m, fft_P=P, alpha=ak * K)
+    ref = oaim.TMOperators(nodes, K, m, P, alpha=ak * K, L=ctx.info()["L"])
+    yield nodes, ctx, ref
+    ctx.close()
+
+
+@pytest.mark.parametrize("op", ["S", "S_alpha", "efie", "efie_alpha"])
+def test_tm_operator_matches_oracle(tm_pair, op):
+    nodes, ctx, ref = tm_pair
+    n = len(nodes)
+    x = synth.random_coeffs(n, 2, seed=3)
+    jk = 1j * K
+    f = {"S": lambda v: ref.Z(v) / jk, "S_alpha": lambda v: ref.Z_alpha(v) / jk, "efie": ref.Z,
+         "efie_alpha": ref.Z_alpha}[op]
+    want = np.stack([f(v) for v in x])
+    got = run_matvec(ctx, op, x)
+    for r in range(2):
+        assert rel(got[r], want[r]) < TOL64, (op, r, rel(got[r], want[r]))
+    got32 = run_matvec(ctx, op, x, precision=1)
+    for r in range(2):
+        assert rel(got32[r], want[r]) < TOL32
+
+
+def test_rhs_planewave_matches_oracle(aimlib):
+    nodes = synth.StarContour.from_seed(3).polygon(10.0, 120)
+    angles = synth.equispaced_angles(4)
+    for form, fn in ((aimlib.TE, dense.te_rhs), (aimlib.TM, dense.tm_rhs)):
+        ctx = aimlib.Context(nodes, K, form, 48)
+        out = torch.empty((4, 120), dtype=torch.complex128, device="cuda:0")
+        ctx.rhs_planewave(angles, out)
+        got = out.cpu().numpy()
+        for r, th in enumerate(angles):
+            assert rel(got[r], fn(nodes, K, th)) < 1e-12
+        ctx.close()
+
+
+def test_host_pointers_match_device_pointers(te_pair):
+    nodes, ctx, ref = te_pair
+    x = synth.random_coeffs(len(nodes), 2, seed=11)
+    y_host = np.empty_like(x)
+    ctx.matvec("calderon_alpha", x, y_host)
+    assert np.array_equal(y_host, run_matvec(ctx, "calderon_alpha", x))
+
+
+# --------------------------------------------------------------------------------------
+# solves
+# --------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def tm_circle(aimlib):
+    nodes = synth.circle_polygon(1.0, 256)
+    ctx = aimlib.Context(nodes, K, aimlib.TM, 64, alpha=8 * K)
+    ref = oaim.TMOperators(nodes, K, 64, 128, alpha=8 * K, L=ctx.info()["L"])
+    yield nodes, ctx, ref
+    ctx.close()
+
+
+def test_tm_circle_solve_matches_oracle_and_series(tm_circle):
+    nodes, ctx, ref = tm_circle
+    E = dense.tm_rhs(nodes, K, 0.0)
+    xo, it, hist = solve.gmres(ref.Z, E, tol=1e-12, restart=100)
+    assert hist[-1] < 1e-11
+    rhs = dev(E[None])
+    x = torch.zeros_like(rhs)
+    info = ctx.solve("efie", rhs, x, tol=1e-11, restart=100, max_iter=3000, check=False)[1]
+    assert info[0]["converged"] == 1, info
+    assert rel(x.cpu().numpy()[0], xo) < 1e-8
+    # against the closed-form series
+    from oracle import special
+    phi = 2 * math.pi * (np.arange(256) + 0.5) / 256
+    assert rel(x.cpu().numpy()[0], special.tm_cylinder_current(phi, K, 1.0)) < 1e-2
+
+
+def test_tm_circle_filtered_solve_residual_under_oracle(tm_circle):
+    nodes, ctx, ref = tm_circle
+    E = dense.tm_rhs(nodes, K, 0.0)
+    rhs = dev(E[None])
+    x = torch.zeros_like(rhs)
+    # the filter leaves modal values ~1e-9 beyond alpha*a: restarted GMRES stalls there, so the
+    # Krylov basis is kept for the whole solve (restart > N)
+    info = ctx.solve("efie_alpha", rhs, x, tol=1e-9, restart=400, max_iter=3000, check=False)[1]
+    assert info[0]["converged"] == 1, info
+    xs = x.cpu().numpy()[0]
+    assert np.linalg.norm(E - ref.Z_alpha(xs)) / np.linalg.norm(E) < 1e-8
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_te_calderon_solve_matches_oracle(te_pair, precision):
+    # unfiltered Calderon (well conditioned, lambda_n mu_n -> 1/4): the solutions agree
+    nodes, ctx, ref = te_pair
+    E = dense.te_rhs(nodes, K, 0.3)
+    b = ref.gram_solve(ref.S(ref.gram_solve(E)))
+    xo, _, _ = solve.gmres(lambda v: ref.calderon(v, False), b, tol=1e-13, restart=100)
+    rhs = dev(E[None])
+    x = torch.zeros_like(rhs)
+    info = ctx.solve("calderon", rhs, x, tol=1e-11, restart=100, precision=precision, inner_tol=1e-5)
+    assert info[0]["converged"] == 1
+    assert rel(x.cpu().numpy()[0], xo) < 1e-8
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_te_filtered_calderon_solve_residual_under_oracle(te_pair, precision):
+    # the filtered system compresses modes beyond alpha*a (Sec. III-B), so it is nearly
+    # singular there and two converged solutions may differ by kappa * tol; what is unique is
+    # that the GPU solution solves the oracle's system: check its residual under the oracle.
+    nodes, ctx, ref = te_pair
+    E = dense.te_rhs(nodes, K, 0.3)
+    b = ref.gram_solve(ref.S_alpha(ref.gram_solve(E)))
+    rhs = dev(E[None])
+    x = torch.zeros_like(rhs)
+    # mixed: FP32-grid refinement contracts the residual by ~kappa*eps_32 per outer step on this
+    # nearly singular system, so it is asked for 1e-8 (its target accuracy is 1e-5)
+    tol = 1e-11 if precision == 0 else 1e-8
+    info = ctx.solve("calderon_alpha", rhs, x, tol=tol, restart=100, max_iter=4000, precision=precision,
+                     inner_tol=1e-5)
+    assert info[0]["converged"] == 1
+    xs = x.cpu().numpy()[0]
+    assert np.linalg.norm(b - ref.calderon(xs, True)) / np.linalg.norm(b) < 100 * tol
