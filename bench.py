@@ -37,7 +37,8 @@ import synth  # noqa: E402
 
 METRIC = "filtered AIM matvec HBM GB/s & solves/s at rel err<=1e-5; served p50/p99 latency"
 UNIT = "solves/s"
-SOLVE_TOL = 1e-8
+SOLVE_TOL = 1e-5
+RESTART = 3000
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal GB300 FP64 rate)
 FALLBACK_HBM_GBS = 6800.0
@@ -46,7 +47,7 @@ FALLBACK_HBM_GBS = 6800.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
@@ -61,7 +62,7 @@ def workload(seed):
 
 def workload_config(wl, precision, world):
     return {"workload": "filtered Calderon TE-EFIE solve, perimeter 1000 wl, N=%d, grid %dx%d (P=%d), s=4, p=4, "
-                        "alpha=2k, 1 rhs, GMRES(50) tol %.0e" % (wl.n, wl.m, wl.m, wl.fft_P, SOLVE_TOL),
+                        "alpha=2k, 1 rhs, GMRES(%d) rel. residual %.0e" % (wl.n, wl.m, wl.m, wl.fft_P, RESTART, SOLVE_TOL),
             "N": wl.n, "grid_m": wl.m, "fft_P": wl.fft_P, "alpha_over_k": wl.alpha / wl.k, "nrhs": 1,
             "precision": precision, "contour_seed": "rank", "ranks": world,
             "l2": "inputs larger than L2 (grid intermediate 3 x 2048 x 4096 complex per product > 129 MB)"}
@@ -170,7 +171,7 @@ def gb300_arm(args):
         ctx = aim.Context(wl.nodes, wl.k, aim.TE, wl.m, fft_P=wl.fft_P, alpha=wl.alpha)
         ctx.rhs_planewave(wl.angles, rhs)
         x.zero_()
-        info = ctx.solve("calderon_alpha", rhs, x, tol=SOLVE_TOL, restart=50, max_iter=2000, precision=prec,
+        info = ctx.solve("calderon_alpha", rhs, x, tol=SOLVE_TOL, restart=RESTART, max_iter=6000, precision=prec,
                          inner_tol=1e-4)
         last["info"] = info[0]
         last["ctx_info"] = ctx.info()
@@ -218,7 +219,7 @@ def gb300_arm(args):
 
     def step_e2e():
         ctx = aim.Context(wl.nodes, wl.k, aim.TE, wl.m, fft_P=wl.fft_P, alpha=wl.alpha)
-        ctx.solve("calderon_alpha", rhs_h, x_h, tol=SOLVE_TOL, restart=50, max_iter=2000, precision=prec,
+        ctx.solve("calderon_alpha", rhs_h, x_h, tol=SOLVE_TOL, restart=RESTART, max_iter=6000, precision=prec,
                   inner_tol=1e-4)
         ctx.close()
 
@@ -314,7 +315,7 @@ def oracle_sample(wl, iters, n_near_rows=64, n_matvec=1):
             "seconds": {"grid_setup": t_grid, "near_field_scaled": t_near, "calderon_product": t_mv}}
 
 
-GPU_ITERS_HINT = 30   # GMRES iterations of the GPU solve of this workload (used by the reference arm)
+GPU_ITERS_HINT = 1831  # GMRES iterations of the GPU solve of this workload (used by the reference arm)
 
 
 def cpu_baseline(wl, iters):

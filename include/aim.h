@@ -90,8 +90,8 @@ typedef struct {
 
 /* Grid (Sec. III-A): m points per side spanning [-L, L]^2, spacing eps = 2L/(m-1).
  * half_side_L <= 0 selects L = R/(1-(s+2)/(m-1)), R = max |vertex coordinate|.
- * fft_P is the circulant embedding side: 0 selects the smallest power of two >= 2m-1;
- * otherwise it must be a power of two with 2m-1 <= fft_P <= 4096. */
+ * fft_P is the circulant embedding side: 0 selects the smallest power of two >= max(2m-1, 64);
+ * otherwise it must be a power of two with max(2m-1, 64) <= fft_P <= 4096. */
 typedef struct {
   int m;
   double half_side_L;

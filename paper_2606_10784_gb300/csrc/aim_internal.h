@@ -53,6 +53,7 @@ struct ProfScope {
 // sizes
 // ------------------------------------------------------------------------------------
 constexpr int kMaxP = 4096;          // largest embedding side (FFT length)
+constexpr int kMinP = 64;            // smallest: every half-length transform has >= 2 passes
 constexpr int kMaxProj = 4;          // TE: phi, phi', n_x phi, n_y phi
 constexpr int kGramBand = 40;        // half bandwidth of the banded G^-1 for large N
 constexpr int kGramDenseMax = 512;   // N at or below which G^-1 is stored dense

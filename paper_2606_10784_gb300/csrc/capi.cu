@@ -256,10 +256,11 @@ aim_status aim_setup(const aim_geometry* geometry, double k, const aim_grid* gri
   ctx->xy.assign(geometry->xy, geometry->xy + 2 * (size_t)geometry->n_seg);
   int P = grid->fft_P;
   if (P == 0) {
-    P = 1;
+    P = kMinP;
     while (P < 2 * grid->m - 1) P *= 2;
   }
   if (P > kMaxP) return fail(AIM_EINVAL, "embedding side P exceeds 4096 (m too large)");
+  if (P < kMinP) return fail(AIM_EINVAL, "embedding side P must be >= 64");
   ctx->P = P;
   ctx->logP = ilog2(P);
   ctx->H = P / 2;
@@ -456,7 +457,7 @@ aim_status aim_query_bytes(const aim_geometry* geometry, const aim_grid* grid, c
   const int n = geometry->n_seg, m = grid->m, s = stencil->s, p = geometry->quad_p;
   int P = grid->fft_P;
   if (P == 0) {
-    P = 1;
+    P = kMinP;
     while (P < 2 * m - 1) P *= 2;
   }
   const size_t H = P / 2;

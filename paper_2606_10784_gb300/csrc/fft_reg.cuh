@@ -1,0 +1,197 @@
+// Register-resident FFT passes for the AIM grid product (Eq. 8 / Eq. 10).
+//
+// A length-H = 2^logH transform (H >= 16) is split into radix-16 passes plus at most one
+// radix-2/4/8 pass (logH = 4q + rem). Each thread owns 16 elements of every transform it works
+// on: one radix-16 butterfly, or 16/R butterflies of a smaller radix. Butterflies follow the
+// Stockham auto-sort indexing (natural order in and out): butterfly b of a pass with current
+// sub-length Ns reads X[b + r H/R], multiplies by W_{Ns R}^{(b mod Ns) r}, does a length-R DFT
+// in registers and writes X[(b - b mod Ns) R + b mod Ns + r Ns].
+// Shared memory holds the exchange between passes, padded by one element every 16 so that
+// the stride-R writes of the first passes do not collide in banks. Twiddles come from the
+// host-computed FP64 table tw[t] = exp(-2 pi i t/P).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+
+namespace aim {
+
+constexpr int kPadShift = 4;
+__host__ __device__ __forceinline__ int padi(int i) { return i + (i >> kPadShift); }
+__host__ __device__ __forceinline__ int padded_len(int H) { return H + (H >> kPadShift); }
+
+template <int R>
+__host__ __device__ constexpr int bitrev_r(int k) {
+  return R == 2 ? k
+       : R == 4 ? ((k & 1) << 1) | ((k >> 1) & 1)
+       : R == 8 ? ((k & 1) << 2) | (k & 2) | ((k >> 2) & 1)
+                : ((k & 1) << 3) | ((k & 2) << 1) | ((k >> 1) & 2) | ((k >> 3) & 1);
+}
+
+// d * W16^e (forward W16 = exp(-2 pi i/16); inverse uses the conjugate), e in [0, 8)
+template <bool INV, typename T2>
+__device__ __forceinline__ T2 rot16(T2 d, int e) {
+  using T = decltype(d.x);
+  constexpr double C1 = 0.92387953251128675613, S1 = 0.38268343236508977173, C2 = 0.70710678118654752440;
+  switch (e) {
+    case 0: return d;
+    case 4: return INV ? mul_plus_i(d) : mul_minus_i(d);
+    default: {
+      double c, s;   // exp(-i 2 pi e/16) = c - i s
+      switch (e) {
+        case 1: c = C1; s = S1; break;
+        case 2: c = C2; s = C2; break;
+        case 3: c = S1; s = C1; break;
+        case 5: c = -S1; s = C1; break;
+        case 6: c = -C2; s = C2; break;
+        default: c = -C1; s = S1; break;   // 7
+      }
+      const T cc = (T)c, ss = INV ? (T)(-s) : (T)s;
+      return T2{d.x * cc + d.y * ss, d.y * cc - d.x * ss};
+    }
+  }
+}
+
+// In-register DFT of length R (2, 4, 8, 16): radix-2 decimation in frequency, then the
+// bit-reversal permutation (resolved at compile time).
+template <int R, bool INV, typename T2>
+__device__ __forceinline__ void dft_reg(T2 (&v)[R]) {
+#pragma unroll
+  for (int len = R; len >= 2; len >>= 1) {
+    const int half = len >> 1;
+#pragma unroll
+    for (int o = 0; o < R; o += len) {
+#pragma unroll
+      for (int i = 0; i < half; ++i) {
+        const T2 a = v[o + i], b = v[o + i + half];
+        v[o + i] = cadd(a, b);
+        v[o + i + half] = rot16<INV>(csub(a, b), i * (16 / len));
+      }
+    }
+  }
+  T2 t[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) t[k] = v[bitrev_r<R>(k)];
+#pragma unroll
+  for (int k = 0; k < R; ++k) v[k] = t[k];
+}
+
+// twiddles W_{Ns R}^{k r}, r = 1..R-1, then the length-R DFT
+template <int LOGR, bool INV, typename T2>
+__device__ __forceinline__ void bfly(T2 (&v)[1 << LOGR], int k, int logNs, const T2* __restrict__ tw, int logP) {
+  constexpr int R = 1 << LOGR;
+  if (k != 0) {
+    const int sh = logP - logNs - LOGR;
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      const T2 w = __ldg(&tw[(k * r) << sh]);
+      v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+    }
+  }
+  dft_reg<R, INV>(v);
+}
+
+__device__ __forceinline__ int fft_npass(int logH) { return (logH >> 2) + ((logH & 3) != 0); }
+__device__ __forceinline__ int fft_logr(int pass, int logH) { return pass < (logH >> 2) ? 4 : (logH & 3); }
+
+// One pass over NF transforms owned by this thread group, shared memory in and out.
+// Each thread works on butterflies b = j + t*tpf (t < 16/R) of each of its transforms, whose
+// padded bases in shared memory are fb[f]. `post(f, out_index, value)` may rewrite a value
+// before it is stored (identity for plain passes). Barrier before and after the stores.
+template <int LOGR, bool INV, int NF, typename T2, typename Post>
+__device__ __forceinline__ void smem_pass(T2* __restrict__ sm, const int (&fb)[NF], int j, int tpf, int logH,
+                                          int logNs, const T2* __restrict__ tw, int logP, Post post) {
+  constexpr int R = 1 << LOGR, NB = 16 >> LOGR;
+  const int lognb = logH - LOGR;
+  const int nsm = (1 << logNs) - 1;
+  T2 v[NF][NB][R];
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const int b = j + t * tpf;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[f][t][r] = sm[fb[f] + padi(b + (r << lognb))];
+      bfly<LOGR, INV>(v[f][t], b & nsm, logNs, tw, logP);
+    }
+  __syncthreads();
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const int b = j + t * tpf;
+      const int k = b & nsm;
+      const int base = ((b - k) << LOGR) + k;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int o = base + (r << logNs);
+        sm[fb[f] + padi(o)] = post(f, o, v[f][t][r]);
+      }
+    }
+  __syncthreads();
+}
+
+// Last pass: shared memory in, `emit(t, r, out_index, values[NF])` out (no stores to shared
+// memory here; callers that write shared memory in `emit` must place a barrier first).
+template <int LOGR, bool INV, int NF, typename T2, typename Emit>
+__device__ __forceinline__ void last_pass(const T2* __restrict__ sm, const int (&fb)[NF], int j, int tpf, int logH,
+                                          int logNs, const T2* __restrict__ tw, int logP, Emit emit) {
+  constexpr int R = 1 << LOGR, NB = 16 >> LOGR;
+  const int lognb = logH - LOGR;
+  const int nsm = (1 << logNs) - 1;
+#pragma unroll
+  for (int t = 0; t < NB; ++t) {
+    const int b = j + t * tpf;
+    const int k = b & nsm;
+    T2 v[NF][R];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[f][r] = sm[fb[f] + padi(b + (r << lognb))];
+      bfly<LOGR, INV>(v[f], k, logNs, tw, logP);
+    }
+    const int base = ((b - k) << LOGR) + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      T2 vals[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) vals[f] = v[f][r];
+      emit(base + (r << logNs), vals);
+    }
+  }
+}
+
+// Runs passes [p0, p1) of a length-2^logH transform in shared memory, dispatching the radix.
+template <bool INV, int NF, typename T2, typename Post>
+__device__ __forceinline__ void smem_passes(T2* sm, const int (&fb)[NF], int j, int tpf, int logH, int p0, int p1,
+                                            int logNs, const T2* tw, int logP, Post post) {
+  for (int p = p0; p < p1; ++p) {
+    const int lr = fft_logr(p, logH);
+    switch (lr) {
+      case 4: smem_pass<4, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, post); break;
+      case 3: smem_pass<3, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, post); break;
+      case 2: smem_pass<2, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, post); break;
+      default: smem_pass<1, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, post); break;
+    }
+    logNs += lr;
+  }
+}
+
+template <bool INV, int NF, typename T2, typename Emit>
+__device__ __forceinline__ void last_pass_dispatch(const T2* sm, const int (&fb)[NF], int j, int tpf, int logH,
+                                                   int logNs, const T2* tw, int logP, Emit emit) {
+  switch (fft_logr(fft_npass(logH) - 1, logH)) {
+    case 4: last_pass<4, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, emit); break;
+    case 3: last_pass<3, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, emit); break;
+    case 2: last_pass<2, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, emit); break;
+    default: last_pass<1, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, emit); break;
+  }
+}
+
+struct Identity {
+  template <typename T2>
+  __device__ __forceinline__ T2 operator()(int, int, T2 v) const { return v; }
+};
+
+}  // namespace aim

@@ -15,16 +15,27 @@
 //               grid points the test projection reads (the restriction [.]_restr).
 //   k_gather    y_i = sum over projections of coef * (P_t^T v)_i plus the near-field row
 //               (C x)_i, one warp per unknown, deterministic.
+// Each length-H transform runs as register-resident radix-16 passes (fft_reg.cuh): the first
+// pass reads its operands straight from global memory (column pass) and the last pass writes
+// straight to global memory, so shared memory carries only the exchanges between passes.
 // The intermediate m x P grid of a channel is stored as column tiles of W entries
 // (W * sizeof(complex) = 32 bytes) so that the column pass reads contiguous blocks and the
 // row passes touch whole 32-byte sectors. Only grid rows that hold active points are stored.
 #include "aim_internal.h"
-#include "fft.cuh"
+#include "fft_reg.cuh"
 
 namespace aim {
 
 template <typename T> using C2 = typename Cplx<T>::type;
 
+// threads per CTA bound: FP64 kernels hold 32 complex128 values per thread in registers
+template <typename T> struct MaxThreads;
+template <> struct MaxThreads<double> { static constexpr int value = 256; };
+template <> struct MaxThreads<float> { static constexpr int value = 512; };
+
+// ------------------------------------------------------------------------------------
+// row pass, forward
+// ------------------------------------------------------------------------------------
 struct RowFwdArgs {
   const double2* x;     // sparse mode: n * nrhs vectors; dense mode: m*m grid per channel
   int dense;
@@ -37,102 +48,171 @@ struct RowFwdArgs {
   void* inter;
   const void* tw;
   int logH, logP, row_lo, nrows;
+  int rows_per_cta;
 };
 
-template <typename T, int NB>
-__global__ void __launch_bounds__(1024) k_row_fwd(RowFwdArgs a) {
+// CTA: rows_per_cta rows of one channel; H/16 threads per row; two transforms per row (a, a w^n).
+template <typename T>
+__global__ void __launch_bounds__(MaxThreads<T>::value) k_row_fwd(RowFwdArgs a) {
   using T2 = C2<T>;
   constexpr int W = TileW<T>::value;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
-  const int H = 1 << a.logH, P = 1 << a.logP;
-  const int rloc = blockIdx.x, iy = a.row_lo + rloc, c = blockIdx.y;
+  const int H = 1 << a.logH, P = 1 << a.logP, tpf = H >> 4, HS = padded_len(H);
+  const int g = threadIdx.x / tpf, j = threadIdx.x - g * tpf;
+  const int rloc = blockIdx.x * a.rows_per_cta + g;
+  const int c = blockIdx.y;
+  const bool live = rloc < a.nrows;
+  const int iy = a.row_lo + rloc;
   const T2* tw = static_cast<const T2*>(a.tw);
-  for (int i = threadIdx.x; i < 2 * H; i += blockDim.x) sm[i] = T2{0, 0};
+  const int fb[2] = {(2 * g) * HS, (2 * g + 1) * HS};
+  // zero the row buffer, then anterpolate u = P_s x into it
+  for (int i = j; i < HS; i += tpf) sm[fb[0] + i] = T2{0, 0};
   __syncthreads();
-  if (a.dense) {
-    const double2* u = a.x + (size_t)c * a.m * a.m + (size_t)iy * a.m;
-    for (int ix = threadIdx.x; ix < a.m; ix += blockDim.x) {
-      const double2 v = u[ix];
-      sm[ix] = T2{(T)v.x, (T)v.y};
-    }
-  } else {
-    const int pj = c / a.nrhs, r = c - pj * a.nrhs;
-    const double* w = a.w[pj];
-    const double2* xv = a.x + (size_t)r * a.n;
-    const int a1 = a.row_ptr[iy + 1];
-    for (int ap = a.row_ptr[iy] + threadIdx.x; ap < a1; ap += blockDim.x) {
-      double re = 0.0, im = 0.0;
-      const int e1 = a.sc_ptr[ap + 1];
-      for (int e = a.sc_ptr[ap]; e < e1; ++e) {
-        const double ww = w[e];
-        const double2 xx = xv[a.sc_col[e]];
-        re = fma(ww, xx.x, re);
-        im = fma(ww, xx.y, im);
+  if (live) {
+    if (a.dense) {
+      const double2* u = a.x + (size_t)c * a.m * a.m + (size_t)iy * a.m;
+      for (int ix = j; ix < a.m; ix += tpf) {
+        const double2 v = u[ix];
+        sm[fb[0] + padi(ix)] = T2{(T)v.x, (T)v.y};
       }
-      sm[a.act_ix[ap]] = T2{(T)re, (T)im};
+    } else {
+      const int pj = c / a.nrhs, r = c - pj * a.nrhs;
+      const double* w = a.w[pj];
+      const double2* xv = a.x + (size_t)r * a.n;
+      const int a1 = a.row_ptr[iy + 1];
+      for (int ap = a.row_ptr[iy] + j; ap < a1; ap += tpf) {
+        double re = 0.0, im = 0.0;
+        const int e1 = a.sc_ptr[ap + 1];
+        for (int e = a.sc_ptr[ap]; e < e1; ++e) {
+          const double ww = w[e];
+          const double2 xx = xv[a.sc_col[e]];
+          re = fma(ww, xx.x, re);
+          im = fma(ww, xx.y, im);
+        }
+        sm[fb[0] + padi(a.act_ix[ap])] = T2{(T)re, (T)im};
+      }
     }
   }
   __syncthreads();
-  for (int nn = threadIdx.x; nn < H; nn += blockDim.x) sm[H + nn] = cmul(sm[nn], tw[nn]);
-  __syncthreads();
-  smem_fft<NB, false>(sm, a.logH, 2, tw, a.logP);
-  T2* out = static_cast<T2*>(a.inter) + (size_t)c * P * a.nrows;
-  for (int q = threadIdx.x; q < P; q += blockDim.x) {
-    const T2 val = (q & 1) ? sm[H + (q >> 1)] : sm[q >> 1];
-    out[((size_t)(q / W) * a.nrows + rloc) * W + (q % W)] = val;
+  // pass 0 (radix 16, Ns = 1) builds both transforms: a and a * w^n
+  {
+    const int lognb = a.logH - 4;
+    T2 va[16], vb[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int nn = j + (r << lognb);
+      va[r] = sm[fb[0] + padi(nn)];
+      vb[r] = cmul(va[r], __ldg(&tw[nn]));
+    }
+    dft_reg<16, false>(va);
+    dft_reg<16, false>(vb);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      sm[fb[0] + padi((j << 4) + r)] = va[r];
+      sm[fb[1] + padi((j << 4) + r)] = vb[r];
+    }
+    __syncthreads();
   }
+  const int np = fft_npass(a.logH);
+  smem_passes<false, 2>(sm, fb, j, tpf, a.logH, 1, np - 1, 4, tw, a.logP, Identity{});
+  int logNs = 0;
+  for (int p = 0; p < np - 1; ++p) logNs += fft_logr(p, a.logH);
+  // last pass: X[2k] = A[k], X[2k+1] = B[k] straight to the tiled intermediate
+  T2* out = static_cast<T2*>(a.inter) + (size_t)c * P * a.nrows;
+  last_pass_dispatch<false, 2>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int k, const T2 (&v)[2]) {
+    if (!live) return;
+    const int q = 2 * k;
+    T2* dst = out + ((size_t)(q / W) * a.nrows + rloc) * W + (q % W);
+    dst[0] = v[0];
+    dst[1] = v[1];
+  });
 }
 
+// ------------------------------------------------------------------------------------
+// column pass: forward DFT x spectrum x inverse DFT
+// ------------------------------------------------------------------------------------
 struct ColArgs {
   void* inter;
   const void* spec;
   const void* tw;
   int logH, logP, row_lo, nrows;
+  int tiles_per_cta;
 };
 
-template <typename T, int NB>
-__global__ void __launch_bounds__(1024) k_col_conv(ColArgs a) {
+// CTA: tiles_per_cta tiles of W columns of one channel; H/16 threads per column, each thread
+// owning the even- and odd-row transforms of its column. Lane order puts the W columns of a
+// row in adjacent lanes, so the global loads and stores of a warp are whole 32-byte sectors.
+template <typename T>
+__global__ void __launch_bounds__(MaxThreads<T>::value) k_col_conv(ColArgs a) {
   using T2 = C2<T>;
   constexpr int W = TileW<T>::value;
   extern __shared__ __align__(16) unsigned char smraw[];
-  T2* sm = reinterpret_cast<T2*>(smraw);   // [w][half][H]
-  const int H = 1 << a.logH, P = 1 << a.logP;
-  const int qt = blockIdx.x, c = blockIdx.y;
+  T2* sm = reinterpret_cast<T2*>(smraw);
+  const int H = 1 << a.logH, P = 1 << a.logP, tpf = H >> 4, HS = padded_len(H);
+  const int per_tile = W * tpf;
+  const int g = threadIdx.x / per_tile, rem = threadIdx.x - g * per_tile;
+  const int w = rem % W, j = rem / W;
+  const int tile = blockIdx.x * a.tiles_per_cta + g;
+  const int c = blockIdx.y;
+  const int colc = g * W + w;
+  const int fb[2] = {(2 * colc) * HS, (2 * colc + 1) * HS};
   const T2* tw = static_cast<const T2*>(a.tw);
-  T2* blk = static_cast<T2*>(a.inter) + (size_t)c * P * a.nrows + (size_t)qt * a.nrows * W;
-  for (int i = threadIdx.x; i < 2 * W * H; i += blockDim.x) sm[i] = T2{0, 0};
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < a.nrows * W; idx += blockDim.x) {
-    const int row = idx / W, w = idx - row * W;
-    sm[(2 * w) * H + a.row_lo + row] = blk[idx];
+  T2* blk = static_cast<T2*>(a.inter) + (size_t)c * P * a.nrows + (size_t)tile * a.nrows * W;
+  const int row_hi = a.row_lo + a.nrows - 1;
+  // pass 0 from global: a[n] and a[n] w^n, n = j + 16-stride
+  {
+    const int lognb = a.logH - 4;
+    T2 va[16], vb[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int nn = j + (r << lognb);
+      const T2 xv = (nn >= a.row_lo && nn <= row_hi) ? blk[(nn - a.row_lo) * W + w] : T2{0, 0};
+      va[r] = xv;
+      vb[r] = cmul(xv, __ldg(&tw[nn]));
+    }
+    dft_reg<16, false>(va);
+    dft_reg<16, false>(vb);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      sm[fb[0] + padi((j << 4) + r)] = va[r];
+      sm[fb[1] + padi((j << 4) + r)] = vb[r];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < W * a.nrows; idx += blockDim.x) {
-    const int w = idx / a.nrows, nn = a.row_lo + (idx - w * a.nrows);
-    sm[(2 * w + 1) * H + nn] = cmul(sm[(2 * w) * H + nn], tw[nn]);
-  }
-  __syncthreads();
-  smem_fft<NB, false>(sm, a.logH, 2 * W, tw, a.logP);
-  const T2* spec = static_cast<const T2*>(a.spec);
-  const int half_h = H >> 1;
-  for (int idx = threadIdx.x; idx < 2 * W * H; idx += blockDim.x) {
-    const int f = idx >> a.logH, kk = idx & (H - 1);
-    const int q = qt * W + (f >> 1);
+  const int np = fft_npass(a.logH);
+  // remaining forward passes; the last one multiplies by the spectrum column before storing
+  smem_passes<false, 2>(sm, fb, j, tpf, a.logH, 1, np - 1, 4, tw, a.logP, Identity{});
+  int logNs = 0;
+  for (int p = 0; p < np - 1; ++p) logNs += fft_logr(p, a.logH);
+  {
+    const int q = tile * W + w;
     const int qq = min(q, P - q);
-    const T2* col = spec + (size_t)qq * (H + 1);
-    const T2 s = (f & 1) ? col[half_h + 1 + min(kk, H - 1 - kk)] : col[min(kk, H - kk)];
-    sm[idx] = cmul(sm[idx], s);
+    const T2* col = static_cast<const T2*>(a.spec) + (size_t)qq * (H + 1);
+    const int half_h = H >> 1;
+    auto spec_mul = [&](int f, int k, T2 v) {
+      const T2 s = f ? __ldg(&col[half_h + 1 + min(k, H - 1 - k)]) : __ldg(&col[min(k, H - k)]);
+      return cmul(v, s);
+    };
+    const int lr = fft_logr(np - 1, a.logH);
+    switch (lr) {
+      case 4: smem_pass<4, false, 2>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, spec_mul); break;
+      case 3: smem_pass<3, false, 2>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, spec_mul); break;
+      case 2: smem_pass<2, false, 2>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, spec_mul); break;
+      default: smem_pass<1, false, 2>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, spec_mul); break;
+    }
   }
-  __syncthreads();
-  smem_fft<NB, true>(sm, a.logH, 2 * W, tw, a.logP);
-  for (int idx = threadIdx.x; idx < a.nrows * W; idx += blockDim.x) {
-    const int row = idx / W, w = idx - row * W;
-    const int nn = a.row_lo + row;
-    blk[idx] = cadd(sm[(2 * w) * H + nn], cmulc(sm[(2 * w + 1) * H + nn], tw[nn]));
-  }
+  // inverse transform; the last pass recombines y[n] = A[n] + conj(w^n) B[n] for kept rows
+  smem_passes<true, 2>(sm, fb, j, tpf, a.logH, 0, np - 1, 0, tw, a.logP, Identity{});
+  last_pass_dispatch<true, 2>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int nn, const T2 (&v)[2]) {
+    if (nn >= a.row_lo && nn <= row_hi) blk[(nn - a.row_lo) * W + w] = cadd(v[0], cmulc(v[1], __ldg(&tw[nn])));
+  });
 }
 
+// ------------------------------------------------------------------------------------
+// row pass, inverse + restriction
+// ------------------------------------------------------------------------------------
 struct RowInvArgs {
   const void* inter;
   const void* tw;
@@ -144,40 +224,100 @@ struct RowInvArgs {
   const int* act_ix;
   int logH, logP, row_lo, nrows;
   double scale;
+  int rows_per_cta;
 };
 
-template <typename T, int NB>
-__global__ void __launch_bounds__(1024) k_row_inv(RowInvArgs a) {
+template <typename T>
+__global__ void __launch_bounds__(MaxThreads<T>::value) k_row_inv(RowInvArgs a) {
   using T2 = C2<T>;
   constexpr int W = TileW<T>::value;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
-  const int H = 1 << a.logH, P = 1 << a.logP;
-  const int rloc = blockIdx.x, iy = a.row_lo + rloc, c = blockIdx.y;
+  const int H = 1 << a.logH, P = 1 << a.logP, tpf = H >> 4, HS = padded_len(H);
+  const int g = threadIdx.x / tpf, j = threadIdx.x - g * tpf;
+  const int rloc = blockIdx.x * a.rows_per_cta + g;
+  const int c = blockIdx.y;
+  const bool live = rloc < a.nrows;
+  const int iy = a.row_lo + rloc;
   const T2* tw = static_cast<const T2*>(a.tw);
+  const int fb[2] = {(2 * g) * HS, (2 * g + 1) * HS};
   const T2* blk = static_cast<const T2*>(a.inter) + (size_t)c * P * a.nrows;
-  for (int q = threadIdx.x; q < P; q += blockDim.x)
-    sm[(q & 1) * H + (q >> 1)] = blk[((size_t)(q / W) * a.nrows + rloc) * W + (q % W)];
-  __syncthreads();
-  smem_fft<NB, true>(sm, a.logH, 2, tw, a.logP);
+  // pass 0 (inverse, radix 16, Ns = 1) from global: A[k] = Y[2k], B[k] = Y[2k+1]
+  {
+    const int lognb = a.logH - 4;
+    T2 va[16], vb[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int k = j + (r << lognb);
+      const int q = 2 * k;
+      if (live) {
+        const T2* src = blk + ((size_t)(q / W) * a.nrows + rloc) * W + (q % W);
+        va[r] = src[0];
+        vb[r] = src[1];
+      } else {
+        va[r] = T2{0, 0};
+        vb[r] = T2{0, 0};
+      }
+    }
+    dft_reg<16, true>(va);
+    dft_reg<16, true>(vb);
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      sm[fb[0] + padi((j << 4) + r)] = va[r];
+      sm[fb[1] + padi((j << 4) + r)] = vb[r];
+    }
+    __syncthreads();
+  }
+  const int np = fft_npass(a.logH);
+  smem_passes<true, 2>(sm, fb, j, tpf, a.logH, 1, np - 1, 4, tw, a.logP, Identity{});
+  int logNs = 0;
+  for (int p = 0; p < np - 1; ++p) logNs += fft_logr(p, a.logH);
   const T sc = (T)a.scale;
   if (a.dense) {
     double2* out = a.dense_out + (size_t)c * a.m * a.m + (size_t)iy * a.m;
-    for (int ix = threadIdx.x; ix < a.m; ix += blockDim.x) {
-      const T2 v = cadd(sm[ix], cmulc(sm[H + ix], tw[ix]));
-      out[ix] = double2{(double)(v.x * sc), (double)(v.y * sc)};
+    last_pass_dispatch<true, 2>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int nn, const T2 (&v)[2]) {
+      if (live && nn < a.m) {
+        const T2 y = cadd(v[0], cmulc(v[1], __ldg(&tw[nn])));
+        out[nn] = double2{(double)(y.x * sc), (double)(y.y * sc)};
+      }
+    });
+    return;
+  }
+  // sparse mode: results into registers, then through shared memory to the active points
+  constexpr int NMAX = 16;   // outputs per thread (16 per transform)
+  T2 ybuf[NMAX];
+  int ycnt = 0;
+  last_pass_dispatch<true, 2>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int nn, const T2 (&v)[2]) {
+    ybuf[ycnt++ & (NMAX - 1)] = cadd(v[0], cmulc(v[1], __ldg(&tw[nn])));
+  });
+  __syncthreads();
+  {
+    // replay the output indices of the last pass to place the values
+    const int lr = fft_logr(np - 1, a.logH);
+    const int R = 1 << lr, NB = 16 >> lr;
+    const int nsm = (1 << logNs) - 1;
+    int q = 0;
+    for (int t = 0; t < NB; ++t) {
+      const int b = j + t * tpf;
+      const int k = b & nsm;
+      const int base = ((b - k) << lr) + k;
+      for (int r = 0; r < R; ++r) sm[fb[0] + padi(base + (r << logNs))] = ybuf[q++];
     }
-  } else {
+  }
+  __syncthreads();
+  if (live) {
     T2* out = static_cast<T2*>(a.vact) + (size_t)c * a.n_act;
     const int a1 = a.row_ptr[iy + 1];
-    for (int ap = a.row_ptr[iy] + threadIdx.x; ap < a1; ap += blockDim.x) {
-      const int ix = a.act_ix[ap];
-      const T2 v = cadd(sm[ix], cmulc(sm[H + ix], tw[ix]));
-      out[ap] = T2{v.x * sc, v.y * sc};
+    for (int ap = a.row_ptr[iy] + j; ap < a1; ap += tpf) {
+      const T2 y = sm[fb[0] + padi(a.act_ix[ap])];
+      out[ap] = T2{y.x * sc, y.y * sc};
     }
   }
 }
 
+// ------------------------------------------------------------------------------------
+// gather + near field, Gram inverse
+// ------------------------------------------------------------------------------------
 struct GatherArgs {
   const void* vact;
   int n_act, n, nrhs, nproj;
@@ -268,18 +408,6 @@ __global__ void k_gram_inv(const double* __restrict__ gi, int blo, int cnt, int 
 // ------------------------------------------------------------------------------------
 // launch configuration
 // ------------------------------------------------------------------------------------
-template <typename T> struct Cfg;
-template <> struct Cfg<double> { static constexpr int NB_ROW = 4, NB_COL = 4; };
-template <> struct Cfg<float> { static constexpr int NB_ROW = 4, NB_COL = 8; };
-
-static int threads_for(int butterflies, int nb) {
-  int t = (butterflies + nb - 1) / nb;
-  t = (t + 31) / 32 * 32;
-  if (t < 64) t = 64;
-  if (t > 1024) t = 1024;
-  return t;
-}
-
 template <typename K>
 static aim_status ensure_smem(K kernel, size_t bytes) {
   if (bytes > 48 * 1024) {
@@ -298,30 +426,38 @@ static aim_status launch_three_passes(aim_ctx* ctx, int channels, bool filtered,
                                       cudaStream_t st) {
   using T2 = C2<T>;
   constexpr int W = TileW<T>::value;
-  const int H = ctx->H;
+  const int H = ctx->H, tpf = H / 16, HS = padded_len(H);
   const T2* tw = std::is_same<T, double>::value ? (const T2*)ctx->tw : (const T2*)ctx->twf;
   const void* spec;
   if (std::is_same<T, double>::value) spec = filtered ? (const void*)ctx->specA : (const void*)ctx->specU;
   else spec = filtered ? (const void*)ctx->specAf : (const void*)ctx->specUf;
   if (channels > 65535) return fail(AIM_EINVAL, "too many channels in one grid pass");
+  if (H < 32) return fail(AIM_EINVAL, "embedding side P must be >= 64");
 
-  // row forward
+  // rows per CTA so that a CTA has at least 128 threads
+  int rpc = 1;
+  while (rpc * tpf < 128 && rpc < ctx->nrows) rpc *= 2;
+  const int row_blocks = (ctx->nrows + rpc - 1) / rpc;
+  const size_t sm_row = 2 * (size_t)rpc * HS * sizeof(T2);
+
   fa.tw = tw;
   fa.logH = ctx->logH;
   fa.logP = ctx->logP;
   fa.row_lo = ctx->row_lo;
   fa.nrows = ctx->nrows;
   fa.inter = ctx->inter;
-  const size_t sm_row = 2 * (size_t)H * sizeof(T2);
-  const int th_row = threads_for(H / 2, Cfg<T>::NB_ROW);
-  AIM_TRY(ensure_smem(k_row_fwd<T, Cfg<T>::NB_ROW>, sm_row));
+  fa.rows_per_cta = rpc;
+  AIM_TRY(ensure_smem(k_row_fwd<T>, sm_row));
   {
     ProfScope ps(K_ROW_FWD, st);
-    k_row_fwd<T, Cfg<T>::NB_ROW><<<dim3(ctx->nrows, channels), th_row, sm_row, st>>>(fa);
+    k_row_fwd<T><<<dim3(row_blocks, channels), rpc * tpf, sm_row, st>>>(fa);
   }
   AIM_CUDA_TRY(cudaGetLastError());
 
   // column pass
+  const int ntiles = ctx->P / W;
+  int tpc = 1;
+  while (tpc * W * tpf < 128 && tpc < ntiles) tpc *= 2;
   ColArgs ca;
   ca.inter = ctx->inter;
   ca.spec = spec;
@@ -330,12 +466,12 @@ static aim_status launch_three_passes(aim_ctx* ctx, int channels, bool filtered,
   ca.logP = ctx->logP;
   ca.row_lo = ctx->row_lo;
   ca.nrows = ctx->nrows;
-  const size_t sm_col = 2 * (size_t)W * H * sizeof(T2);
-  const int th_col = threads_for(W * H / 2, Cfg<T>::NB_COL);
-  AIM_TRY(ensure_smem(k_col_conv<T, Cfg<T>::NB_COL>, sm_col));
+  ca.tiles_per_cta = tpc;
+  const size_t sm_col = 2 * (size_t)tpc * W * HS * sizeof(T2);
+  AIM_TRY(ensure_smem(k_col_conv<T>, sm_col));
   {
     ProfScope ps(K_COL_CONV, st);
-    k_col_conv<T, Cfg<T>::NB_COL><<<dim3(ctx->P / W, channels), th_col, sm_col, st>>>(ca);
+    k_col_conv<T><<<dim3(ntiles / tpc, channels), tpc * W * tpf, sm_col, st>>>(ca);
   }
   AIM_CUDA_TRY(cudaGetLastError());
 
@@ -347,10 +483,11 @@ static aim_status launch_three_passes(aim_ctx* ctx, int channels, bool filtered,
   ia.row_lo = ctx->row_lo;
   ia.nrows = ctx->nrows;
   ia.scale = 1.0 / ((double)ctx->P * (double)ctx->P);
-  AIM_TRY(ensure_smem(k_row_inv<T, Cfg<T>::NB_ROW>, sm_row));
+  ia.rows_per_cta = rpc;
+  AIM_TRY(ensure_smem(k_row_inv<T>, sm_row));
   {
     ProfScope ps(K_ROW_INV, st);
-    k_row_inv<T, Cfg<T>::NB_ROW><<<dim3(ctx->nrows, channels), th_row, sm_row, st>>>(ia);
+    k_row_inv<T><<<dim3(row_blocks, channels), rpc * tpf, sm_row, st>>>(ia);
   }
   AIM_CUDA_TRY(cudaGetLastError());
   return AIM_OK;

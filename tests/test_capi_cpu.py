@@ -58,7 +58,8 @@ def test_query_bytes_is_host_only_and_scales(lib):
 def test_setup_rejects_bad_arguments_before_touching_the_gpu(lib):
     from paper_2606_10784_gb300 import aim
     nodes = synth.circle_polygon(1.0, 64)
-    for kw, status in ((dict(m=4), aim.EINVAL), (dict(m=32, fft_P=48), aim.EINVAL), (dict(m=32, s=1), aim.EINVAL),
+    for kw, status in ((dict(m=4), aim.EINVAL), (dict(m=32, fft_P=48), aim.EINVAL), (dict(m=16, fft_P=32), aim.EINVAL),
+                       (dict(m=32, s=1), aim.EINVAL),
                        (dict(m=32, alpha=1.0), aim.EINVAL)):
         with pytest.raises(aim.AimError) as exc:
             aim.Context(nodes, 2 * np.pi, aim.TE, **kw)

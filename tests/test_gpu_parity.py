@@ -51,8 +51,8 @@ def run_matvec(ctx, op, x, precision=0):
 # --------------------------------------------------------------------------------------
 # grid product alone (Eq. 8 bracket, Eq. 10 bracket)
 # --------------------------------------------------------------------------------------
-@pytest.mark.parametrize("m,P,alpha_k,radius", [(16, 32, 3.0, 1.0), (24, 64, 4.0, 1.0), (64, 128, 8.0, 1.0),
-                                                (128, 256, 2.0, 8.0)])
+@pytest.mark.parametrize("m,P,alpha_k,radius", [(16, 64, 3.0, 1.0), (24, 64, 4.0, 1.0), (64, 128, 8.0, 1.0),
+                                                (32, 256, 4.0, 1.0), (128, 256, 2.0, 8.0)])
 def test_grid_product_matches_oracle(aimlib, m, P, alpha_k, radius):
     # radius 8 puts kernel samples at k r up to ~150 (the large-argument Bessel branch)
     nodes = synth.circle_polygon(radius, 96 if radius < 2 else 400)
@@ -245,8 +245,9 @@ def test_te_filtered_calderon_solve_residual_under_oracle(te_pair, precision):
     x = torch.zeros_like(rhs)
     # mixed: FP32-grid refinement contracts the residual by ~kappa*eps_32 per outer step on this
     # nearly singular system, so it is asked for 1e-8 (its target accuracy is 1e-5)
-    tol = 1e-11 if precision == 0 else 1e-8
-    info = ctx.solve("calderon_alpha", rhs, x, tol=tol, restart=100, max_iter=4000, precision=precision,
+    tol = 1e-10 if precision == 0 else 1e-8
+    # full GMRES (restart > N): restarted GMRES stalls on the compressed modes
+    info = ctx.solve("calderon_alpha", rhs, x, tol=tol, restart=1000, max_iter=4000, precision=precision,
                      inner_tol=1e-5)
     assert info[0]["converged"] == 1
     xs = x.cpu().numpy()[0]
