@@ -50,7 +50,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "native"], default="fp64",
+                    help="fp64: FP64-accurate double-float grid arithmetic; mixed: complex64 grid with FP64 "
+                         "refinement; native: IEEE binary64 grid arithmetic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
     return ap.parse_args()
@@ -128,22 +130,72 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
+# Flop costs of one complex operation in the kernels' own arithmetic (FMA = 2 flops).
+# Plain complex64/complex128: add 2, multiply 6. Double-float (each real an unevaluated sum of two
+# floats): an add is TwoSum (6) + 2 adds + FastTwoSum (3) = 11 per real part, so 22 per complex
+# add; a multiply's real part is two exact products (1 mul + 1 fma each = 6), TwoSum (6), 2 adds,
+# 4 cross-term fmas (8) and FastTwoSum (3) = 25, so 50 per complex multiply.
+CPLX_COST = {"plain": (2, 6), "df": (22, 50)}
+
+
+def fft_flops(logh: int, kind: str) -> float:
+    """Flops of one length-2^logh transform as the kernels run it: radix-16 passes (radix-2
+    decimation in frequency inside, 10 non-trivial rotations per 16-point DFT) plus one radix-2^r
+    pass; every pass but the first multiplies by R-1 twiddles, of which 11/4/1 (R = 16/8/4) are
+    formed as products of table powers."""
+    add, mul = CPLX_COST[kind]
+    h = 1 << logh
+
+    def dft(r):
+        lg = int(math.log2(r))
+        rot = {16: 10, 8: 2, 4: 0, 2: 0}[r]
+        return (r // 2) * lg * 2 * add + rot * mul
+
+    extra = {16: 11, 8: 4, 4: 1, 2: 0}
+    radices = [16] * (logh // 4) + ([1 << (logh % 4)] if logh % 4 else [])
+    total = 0.0
+    for p, r in enumerate(radices):
+        per = dft(r) + (0 if p == 0 else (r - 1 + extra[r]) * mul)
+        total += (h // r) * per
+    return total
+
+
 def col_conv_algorithmic(wl, info, precision, channels):
     """Algorithmic work of one column-pass launch (the dominant kernel).
 
     Bytes: each channel's m_rows x P intermediate read once and written once, plus the stored
-    (P/2+1)^2 spectrum read once per launch. Flops (5 n log2 n per complex n-point FFT): per
-    column and channel four half-length FFTs, the twiddle of the odd half, the spectral
-    product of P points and the recombination of the kept rows.
+    (P/2+1)^2 spectrum read once per channel. Flops: per column and channel four half-length
+    transforms (fft_flops), the w^n twiddle of the odd half, the spectral product of P points
+    and the recombination y = A + conj(w^n) B at every one of the H rows.
     """
     P = wl.fft_P
     H = P // 2
     rows = info["row_hi"] - info["row_lo"] + 1
-    b = 16 if precision == "fp64" else 8
-    bytes_ = channels * 2 * rows * P * b + (H + 1) ** 2 * b
-    per_col = 4 * 5 * H * math.log2(H) + 6 * rows + 6 * P + 8 * rows
+    kind = "df" if precision == "fp64" else "plain"
+    add, mul = CPLX_COST[kind]
+    b = 8 if precision == "mixed" else 16
+    bytes_ = channels * (2 * rows * P * b + (H + 1) ** 2 * b)
+    per_col = 4 * fft_flops(int(math.log2(H)), kind) + H * mul + P * mul + H * (mul + add)
     flops = channels * P * per_col
     return bytes_, flops
+
+
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz = 80.5
+
+
+def aggregate(elapsed: float, steps: int, world: int, device=None):
+    """Max-over-ranks elapsed time and the whole-job rate (all ranks' steps / that time).
+
+    Each rank works on its own problem (weak scaling), so the only exchange is this one
+    reduction of a scalar; with world == 1 nothing is communicated.
+    """
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    return elapsed, steps * world / elapsed
 
 
 def gb300_arm(args):
@@ -161,7 +213,7 @@ def gb300_arm(args):
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    prec = aim.FP64 if args.precision == "fp64" else aim.MIXED
+    prec = {"fp64": aim.FP64, "mixed": aim.MIXED, "native": aim.FP64_NATIVE}[args.precision]
     wl = workload(args.seed + rank)
     rhs = torch.empty((1, wl.n), dtype=torch.complex128, device=dev)
     x = torch.zeros_like(rhs)
@@ -204,12 +256,7 @@ def gb300_arm(args):
     launches = aim.launch_count() - l0
     prof = aim.profile_stop()
     clocks = sampler.stop()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
-    value = args.steps * world / elapsed
+    elapsed, value = aggregate(elapsed, args.steps, world, dev)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
     rhs_h = torch.empty((1, wl.n), dtype=torch.complex128, pin_memory=True)
@@ -230,14 +277,11 @@ def gb300_arm(args):
     for _ in range(args.steps):
         step_e2e()
     torch.cuda.synchronize()
-    e2e_el = time.perf_counter() - t0
+    e2e_el, e2e_value = aggregate(time.perf_counter() - t0, args.steps, world, dev)
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([e2e_el], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_el = float(t.item())
         dist.destroy_process_group()
-    e2e = {"value": args.steps * world / e2e_el, "unit": UNIT,
+    e2e = {"value": e2e_value, "unit": UNIT,
            "h2d_bytes_per_step": int(wl.nodes.nbytes + rhs_h.numel() * 16),
            "d2h_bytes_per_step": int(x_h.numel() * 16)}
 
@@ -257,11 +301,17 @@ def gb300_arm(args):
         b1, f1 = col_conv_algorithmic(wl, info, args.precision, 1)
         per_launch_bytes = (b3 + b1) / 2
         per_launch_flops = (f3 + f1) / 2
-        if args.precision == "fp64":
+        if args.precision in ("fp64", "native"):
+            # FP64 mode runs double-float arithmetic on the FP32 pipe; native mode the FP64 pipe
+            peak = FP32_PEAK_TFLOPS if args.precision == "fp64" else FP64_PEAK_TFLOPS
             ach = per_launch_flops / avg_s / 1e12
-            roof = {"bound": "alu", "kernel": name, "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
-                    "peak_source": "FP64 nominal: 152 SMs x 64 FP64 flop/clk x 2.07 GHz (MEASURED_PEAKS has no FP64)",
+            roof = {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                    "frac": ach / peak, "traffic": None,
+                    "peak_source": ("FP32 pipe nominal: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived; "
+                                    "MEASURED_PEAKS has no FP32 figure); flops counted in double-float arithmetic"
+                                    if args.precision == "fp64" else
+                                    "FP64 nominal: 152 SMs x 64 FP64 flop/clk x 2.07 GHz (derived)"),
+                    "algorithmic_flops_per_launch": per_launch_flops,
                     "algorithmic_bytes_per_launch": per_launch_bytes,
                     "hbm_frac_of_measured": per_launch_bytes / avg_s / 1e9 / peaks["hbm_gbs"],
                     "launches": nl, "avg_launch_ms": avg_s * 1e3}
@@ -273,7 +323,9 @@ def gb300_arm(args):
     kernels = {k: {"launches": v[0], "total_ms": round(v[1], 3)} for k, v in prof.items()}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": max(3, args.warmup), "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "c128" if args.precision == "fp64" else "c64+f64",
+           "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "df64 (complex fp32-pair double-float grid; c128 vectors, f64 Arnoldi)",
+                                                   "mixed": "c64 grid + f64 refinement",
+                                                   "native": "c128"}[args.precision],
            "data": "synthetic (seeded random smooth contour family)",
            "config": workload_config(wl, args.precision, world), "e2e": e2e, "gpu_launches": launches,
            "roofline": roof, "clocks": clocks, "solve": last["info"],

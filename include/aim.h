@@ -25,9 +25,8 @@
  * Conventions
  *   - Lengths and the wavenumber k share one unit; time dependence e^{+j w t};
  *     g(r) = -(j/4) H0^(2)(k r); eta = 1.
- *   - Complex vectors are interleaved (re, im). precision 0 (AIM_FP64): complex128;
- *     precision 1 (AIM_MIXED): the grid FFT products and the near-field SpMV run in
- *     complex64 while the vectors a caller passes stay complex128.
+ *   - Complex vectors are interleaved (re, im) complex128 in every precision mode; the mode
+ *     (AIM_FP64, AIM_MIXED, AIM_FP64_NATIVE, below) selects the grid arithmetic only.
  *   - Multi-vector arguments are column-major: vector r of nrhs starts at element r*n.
  *   - Vector pointers may be device memory or host memory (pageable or pinned); the
  *     library detects which (cudaPointerGetAttributes) and stages host data through
@@ -76,7 +75,14 @@ typedef enum {
   AIM_OP_EFIE_ALPHA = 7       /* TM only: j k eta S^alpha */
 } aim_op;
 
-enum { AIM_FP64 = 0, AIM_MIXED = 1 };
+/* Grid arithmetic of a product (vectors are complex128 in every mode):
+ *   AIM_FP64        FP64-accurate (relative rounding ~2^-48 per operation): double-float
+ *                   arithmetic on the FP32 pipe, since GB300's FP64 pipe is ~1/58 of its FP32
+ *                   pipe; grid intermediates are 16 bytes per complex.
+ *   AIM_MIXED       complex64 grid products and near-field SpMV (FP32 arithmetic).
+ *   AIM_FP64_NATIVE IEEE binary64 grid arithmetic on the FP64 pipe (the reference the other
+ *                   two are tested against). */
+enum { AIM_FP64 = 0, AIM_MIXED = 1, AIM_FP64_NATIVE = 2 };
 
 /* Geometry: a closed polygon, counter-clockwise, given by its n_seg vertices (x0,y0,x1,y1,...).
  * Segment e joins vertex e to vertex e+1 (mod n_seg). The unknowns are one per segment (TM)
@@ -117,7 +123,8 @@ typedef struct {
   int restart;         /* GMRES restart length (1..10000); the Krylov basis takes
                           (restart+4) * n * nrhs * 16 bytes of device memory */
   int max_iter;        /* total inner iterations per right-hand side */
-  int precision;       /* AIM_FP64 or AIM_MIXED (FP32 grid + FP64 iterative refinement) */
+  int precision;       /* AIM_FP64, AIM_FP64_NATIVE, or AIM_MIXED (FP32 grid inner solves inside
+                          iterative refinement with AIM_FP64 residuals) */
   double inner_tol;    /* mixed only: relative tolerance of each inner FP32-grid solve (e.g. 1e-4) */
   int timeout_ms;      /* <= 0: no limit */
 } aim_solve_opts;
@@ -163,6 +170,14 @@ aim_status aim_get_info(const aim_ctx* ctx, aim_info* info);
 /* Pre-allocates workspaces for up to nrhs simultaneous vectors in the given precision,
  * so that later calls (and CUDA-graph capture of them) allocate nothing. */
 aim_status aim_reserve(aim_ctx* ctx, int nrhs, int precision);
+
+/* Autotuner (no counterpart in the paper; a launch-schedule choice). Times the filtered
+ * product (S^alpha) for nrhs vectors under each candidate schedule of the grid kernels -
+ * one or two transforms per thread, 128 or 256 threads per row-pass CTA - and keeps the
+ * fastest for this context and precision. Results are identical under every schedule
+ * (same arithmetic, same order). Synchronises `stream`. *chosen (host, may be NULL)
+ * receives tpt * 1000 + row threads of the winner. */
+aim_status aim_autotune(aim_ctx* ctx, int nrhs, int precision, void* stream, int* chosen);
 
 /* Right-hand sides for unit plane waves exp(-j k khat.r), khat = (cos th, sin th):
  * TE: E_i = <phi_i, (jk/eta) E_t> with E^i = eta H^i_z (z x khat) (Sec. II, below Eq. 2);

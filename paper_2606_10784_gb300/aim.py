@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(HERE, "libaimgb300.so")
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENUMERIC, ETIMEOUT, ESTATE = range(8)
 TM, TE = 0, 1
 OP_S, OP_S_ALPHA, OP_N, OP_CALDERON, OP_CALDERON_ALPHA, OP_GRAM_INV, OP_EFIE, OP_EFIE_ALPHA = range(8)
-FP64, MIXED = 0, 1
+FP64, MIXED, FP64_NATIVE = 0, 1, 2
 
 OPS = {"S": OP_S, "S_alpha": OP_S_ALPHA, "N": OP_N, "calderon": OP_CALDERON,
        "calderon_alpha": OP_CALDERON_ALPHA, "gram_inv": OP_GRAM_INV, "efie": OP_EFIE, "efie_alpha": OP_EFIE_ALPHA}
@@ -115,6 +115,8 @@ def lib() -> ctypes.CDLL:
     L.aim_query_bytes.argtypes = [ctypes.POINTER(Geometry), ctypes.POINTER(Grid), ctypes.POINTER(Stencil), i, i,
                                   ctypes.POINTER(ctypes.c_size_t)]
     L.aim_query_bytes.restype = i
+    L.aim_autotune.argtypes = [vp, i, i, vp, ctypes.POINTER(i)]
+    L.aim_autotune.restype = i
     L.aim_launch_count.argtypes = []
     L.aim_launch_count.restype = ctypes.c_longlong
     L.aim_profile_start.argtypes = []
@@ -219,6 +221,13 @@ class Context:
 
     def reserve(self, nrhs: int, precision: int = FP64):
         _check(lib().aim_reserve(self._h, int(nrhs), int(precision)), "aim_reserve")
+
+    def autotune(self, nrhs: int = 1, precision: int = FP64, stream=None) -> dict:
+        """Pick the fastest launch schedule for this context; returns it."""
+        chosen = ctypes.c_int(0)
+        _check(lib().aim_autotune(self._h, int(nrhs), int(precision), _stream_ptr(stream), ctypes.byref(chosen)),
+               "aim_autotune")
+        return {"transforms_per_thread": chosen.value // 1000, "min_row_threads": chosen.value % 1000}
 
     def rhs_planewave(self, angles, out, stream=None):
         ang = np.ascontiguousarray(np.asarray(angles, dtype=np.float64).reshape(-1))

@@ -11,6 +11,8 @@
 
 namespace aim {
 
+struct dfc;   // double-float complex (dfloat.cuh)
+
 // ------------------------------------------------------------------------------------
 // error plumbing
 // ------------------------------------------------------------------------------------
@@ -92,6 +94,13 @@ struct NearField {
   long long nnz = 0;
 };
 
+// Launch schedule of the grid kernels for one precision: transforms per thread (1: even/odd
+// halves in adjacent lanes, 2: both in one thread) and the minimum threads of a row-pass CTA.
+struct Schedule {
+  int tpt;
+  int min_row_threads;
+};
+
 // operator selection for one batched grid pass
 struct PassSpec {
   int nproj;                       // projections applied to each rhs (N: 3, S: 1)
@@ -123,8 +132,11 @@ struct aim_ctx {
   double2* specA = nullptr;
   float2* specUf = nullptr;
   float2* specAf = nullptr;
+  float4* specUdf = nullptr;   // double-float copies (re hi, re lo, im hi, im lo)
+  float4* specAdf = nullptr;
   double2* tw = nullptr;    // e^{-2 pi i t / P}, t < P
   float2* twf = nullptr;
+  float4* twdf = nullptr;
   // Gram inverse, row i: entries for columns (i + d) mod n, d = -band..band
   double* gram_inv = nullptr;
   int gram_band = 0;
@@ -139,7 +151,9 @@ struct aim_ctx {
   double2* kry = nullptr; size_t kry_bytes = 0;        // GMRES workspace
   double* red = nullptr; size_t red_bytes = 0;          // reduction scratch (dot products)
   double* red_host = nullptr; size_t red_host_bytes = 0;
-  int reserved_rhs[2] = {0, 0};
+  int reserved_rhs[3] = {0, 0, 0};   // per precision (AIM_FP64, AIM_MIXED, AIM_FP64_NATIVE)
+  // launch schedule per precision; defaults measured on GB300, aim_autotune re-measures
+  aim::Schedule sched[3] = {{1, 128}, {2, 128}, {2, 128}};
   // bookkeeping
   std::vector<void*> allocations;
   size_t device_bytes = 0;

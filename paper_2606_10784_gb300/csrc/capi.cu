@@ -65,7 +65,7 @@ static aim_status grow(void** buf, size_t* have, size_t need) {
 
 aim_status reserve(aim_ctx* ctx, int nrhs, int precision) {
   if (nrhs < 1) return fail(AIM_EINVAL, "nrhs must be >= 1");
-  const int pidx = precision == AIM_MIXED ? 1 : 0;
+  const int pidx = precision;
   const int chan = (ctx->form == AIM_TE_P1_GALERKIN ? 3 : 1) * nrhs;
   const size_t el = precision == AIM_MIXED ? sizeof(float2) : sizeof(double2);
   AIM_TRY(grow(&ctx->inter, &ctx->inter_bytes, inter_bytes_needed(ctx, chan, precision)));
@@ -138,14 +138,14 @@ static PassSpec make_spec(const aim_ctx* ctx, aim_op op) {
 
 static aim_status pass(aim_ctx* ctx, aim_op op, int nrhs, const double2* x, double2* y, int precision, cudaStream_t st) {
   const PassSpec spec = make_spec(ctx, op);
-  if (precision == AIM_MIXED) return grid_pass<float>(ctx, spec, nrhs, x, y, st);
-  return grid_pass<double>(ctx, spec, nrhs, x, y, st);
+  if (precision == AIM_MIXED) return grid_pass<float2>(ctx, spec, nrhs, x, y, st);
+  if (precision == AIM_FP64_NATIVE) return grid_pass<double2>(ctx, spec, nrhs, x, y, st);
+  return grid_pass<dfc>(ctx, spec, nrhs, x, y, st);
 }
 
 aim_status apply_op(aim_ctx* ctx, aim_op op, int nrhs, const double2* x, double2* y, int precision, cudaStream_t st) {
   const bool te = ctx->form == AIM_TE_P1_GALERKIN;
-  const int pidx = precision == AIM_MIXED ? 1 : 0;
-  if (ctx->reserved_rhs[pidx] < nrhs) AIM_TRY(reserve(ctx, nrhs, precision));
+  if (ctx->reserved_rhs[precision] < nrhs) AIM_TRY(reserve(ctx, nrhs, precision));
   switch (op) {
     case AIM_OP_S:
     case AIM_OP_S_ALPHA:
@@ -299,8 +299,15 @@ aim_status aim_setup(const aim_geometry* geometry, double k, const aim_grid* gri
     tw[t] = double2{hs.tw[2 * t], hs.tw[2 * t + 1]};
     twf[t] = float2{(float)hs.tw[2 * t], (float)hs.tw[2 * t + 1]};
   }
+  std::vector<float4> twdf(P);
+  for (int t = 0; t < P; ++t) {
+    const double c = hs.tw[2 * t], s = hs.tw[2 * t + 1];
+    const float ch = (float)c, sh = (float)s;
+    twdf[t] = float4{ch, (float)(c - (double)ch), sh, (float)(s - (double)sh)};
+  }
   AIM_TRY(upload(ctx, &ctx->tw, tw, st));
   AIM_TRY(upload(ctx, &ctx->twf, twf, st));
+  AIM_TRY(upload(ctx, &ctx->twdf, twdf, st));
   if (!hs.gram_inv.empty()) {
     AIM_TRY(upload(ctx, &ctx->gram_inv, hs.gram_inv, st));
     ctx->gram_band = hs.gram_band;
@@ -336,8 +343,51 @@ aim_status aim_get_info(const aim_ctx* ctx, aim_info* info) {
 
 aim_status aim_reserve(aim_ctx* ctx, int nrhs, int precision) {
   if (!ctx) return fail(AIM_EINVAL, "null context");
-  if (precision != AIM_FP64 && precision != AIM_MIXED) return fail(AIM_EINVAL, "precision must be 0 or 1");
+  if (precision < AIM_FP64 || precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "precision must be 0, 1 or 2");
   return reserve(ctx, nrhs, precision);
+}
+
+aim_status aim_autotune(aim_ctx* ctx, int nrhs, int precision, void* stream, int* chosen) {
+  if (!ctx || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
+  if (precision < AIM_FP64 || precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "precision must be 0, 1 or 2");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  AIM_TRY(reserve(ctx, nrhs, precision));
+  const size_t bytes = (size_t)ctx->n * nrhs * sizeof(double2);
+  AIM_TRY(stage(ctx, bytes, bytes));
+  AIM_CUDA_TRY(cudaMemsetAsync(ctx->stage_in, 0, bytes, st));
+  cudaEvent_t e0, e1;
+  AIM_CUDA_TRY(cudaEventCreate(&e0));
+  AIM_CUDA_TRY(cudaEventCreate(&e1));
+  const Schedule saved = ctx->sched[precision];
+  Schedule best = saved;
+  float best_ms = 1e30f;
+  const int tpts[2] = {1, 2};
+  const int rows[2] = {128, 256};
+  aim_status s = AIM_OK;
+  for (int a = 0; a < 2 && s == AIM_OK; ++a) {
+    if (precision == AIM_FP64_NATIVE && tpts[a] == 1) continue;   // native FP64 keeps two per thread
+    for (int b = 0; b < 2 && s == AIM_OK; ++b) {
+      ctx->sched[precision] = Schedule{tpts[a], rows[b]};
+      s = apply_op(ctx, AIM_OP_S_ALPHA, nrhs, ctx->stage_in, ctx->stage_out, precision, st);   // warm
+      if (s != AIM_OK) break;
+      cudaEventRecord(e0, st);
+      for (int it = 0; it < 3 && s == AIM_OK; ++it)
+        s = apply_op(ctx, AIM_OP_S_ALPHA, nrhs, ctx->stage_in, ctx->stage_out, precision, st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { s = fail(AIM_ECUDA, "autotune event"); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = ctx->sched[precision];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->sched[precision] = s == AIM_OK ? best : saved;
+  if (chosen) *chosen = ctx->sched[precision].tpt * 1000 + ctx->sched[precision].min_row_threads;
+  return s;
 }
 
 aim_status aim_rhs_planewave(aim_ctx* ctx, int nrhs, const double* angles, void* rhs, void* stream) {
@@ -362,7 +412,7 @@ aim_status aim_rhs_planewave(aim_ctx* ctx, int nrhs, const double* angles, void*
 
 aim_status aim_matvec(aim_ctx* ctx, aim_op op, int nrhs, const void* x, void* y, int precision, void* stream) {
   if (!ctx || !x || !y || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
-  if (precision != AIM_FP64 && precision != AIM_MIXED) return fail(AIM_EINVAL, "precision must be 0 or 1");
+  if (precision < AIM_FP64 || precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "precision must be 0, 1 or 2");
   if (x == y) return fail(AIM_EINVAL, "x and y must not overlap");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)ctx->n * nrhs * sizeof(double2);
@@ -384,7 +434,7 @@ aim_status aim_matvec(aim_ctx* ctx, aim_op op, int nrhs, const void* x, void* y,
 
 aim_status aim_grid_product(aim_ctx* ctx, int filtered, int nrhs, const void* u, void* v, int precision, void* stream) {
   if (!ctx || !u || !v || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
-  if (precision != AIM_FP64 && precision != AIM_MIXED) return fail(AIM_EINVAL, "precision must be 0 or 1");
+  if (precision < AIM_FP64 || precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "precision must be 0, 1 or 2");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)ctx->m * ctx->m * nrhs * sizeof(double2);
   const bool du = device_pointer(u), dv = device_pointer(v);
@@ -398,8 +448,9 @@ aim_status aim_grid_product(aim_ctx* ctx, int filtered, int nrhs, const void* u,
     uin = ctx->stage_in;
   }
   double2* vout = dv ? static_cast<double2*>(v) : ctx->stage_out;
-  if (precision == AIM_MIXED) AIM_TRY(grid_product_dense<float>(ctx, filtered != 0, nrhs, uin, vout, st));
-  else AIM_TRY(grid_product_dense<double>(ctx, filtered != 0, nrhs, uin, vout, st));
+  if (precision == AIM_MIXED) AIM_TRY(grid_product_dense<float2>(ctx, filtered != 0, nrhs, uin, vout, st));
+  else if (precision == AIM_FP64_NATIVE) AIM_TRY(grid_product_dense<double2>(ctx, filtered != 0, nrhs, uin, vout, st));
+  else AIM_TRY(grid_product_dense<dfc>(ctx, filtered != 0, nrhs, uin, vout, st));
   if (!dv) {
     AIM_CUDA_TRY(cudaMemcpyAsync(v, vout, bytes, cudaMemcpyDeviceToHost, st));
     AIM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -412,7 +463,7 @@ aim_status aim_solve(aim_ctx* ctx, aim_op system, int nrhs, const void* rhs, voi
   if (!ctx || !rhs || !x || !opts || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
   if (!(opts->tol > 0.0) || opts->restart < 1 || opts->restart > 10000 || opts->max_iter < 1)
     return fail(AIM_EINVAL, "bad solver options");
-  if (opts->precision != AIM_FP64 && opts->precision != AIM_MIXED) return fail(AIM_EINVAL, "bad precision");
+  if (opts->precision < AIM_FP64 || opts->precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "bad precision");
   const bool te = ctx->form == AIM_TE_P1_GALERKIN;
   if (system != AIM_OP_EFIE && system != AIM_OP_EFIE_ALPHA && system != AIM_OP_CALDERON && system != AIM_OP_CALDERON_ALPHA)
     return fail(AIM_EINVAL, "system must be EFIE, EFIE_ALPHA, CALDERON or CALDERON_ALPHA");
@@ -423,7 +474,7 @@ aim_status aim_solve(aim_ctx* ctx, aim_op system, int nrhs, const void* rhs, voi
   const size_t bytes = (size_t)ctx->n * nrhs * sizeof(double2);
   const bool dr = device_pointer(rhs), dx = device_pointer(x);
   AIM_TRY(reserve(ctx, nrhs, AIM_FP64));
-  if (opts->precision == AIM_MIXED) AIM_TRY(reserve(ctx, nrhs, AIM_MIXED));
+  if (opts->precision != AIM_FP64) AIM_TRY(reserve(ctx, nrhs, opts->precision));
   AIM_TRY(stage(ctx, bytes, bytes));
   // b lives in stage_in (for Calderon systems: G^-1 S G^-1 E); x in place or staged
   double2* b = ctx->stage_in;

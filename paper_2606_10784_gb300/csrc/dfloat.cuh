@@ -1,0 +1,127 @@
+// Double-float complex arithmetic: FP64-class accuracy on the FP32 pipe.
+//
+// GB300's FP64 rate is about 1/58 of its FP32 rate, so the FP64-accurate grid product runs its
+// FFTs in "double-float" arithmetic: every real value is an unevaluated sum hi + lo of two
+// floats with |lo| <= ulp(hi)/2 (T. J. Dekker, "A floating-point technique for extending the
+// available precision", 1971). Sums use Knuth's error-free TwoSum, products the FMA-based
+// exact product a*b = p + fma(a, b, -p). The relative error of one operation is about 2^-48
+// (sums are accurate relative to |a|+|b|, which is what the normwise error bound of an FFT
+// needs). Every operation is written with explicit round-to-nearest intrinsics so that the
+// compiler cannot contract or reassociate the error-free transformations.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace aim {
+
+struct __align__(16) dfc {
+  float xh, xl, yh, yl;   // re = xh + xl, im = yh + yl
+};
+
+__device__ __forceinline__ void ef_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ void ef_fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// (ah + al) + (bh + bl)
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& rh, float& rl) {
+  float s, e;
+  ef_two_sum(ah, bh, s, e);
+  e = __fadd_rn(e, __fadd_rn(al, bl));
+  ef_fast_two_sum(s, e, rh, rl);
+}
+
+// (ah + al)(bh + bl) - (ch + cl)(dh + dl)  (sign = -1)  or  ... + ...  (sign = +1)
+template <int SIGN>
+__device__ __forceinline__ void df_dot2(float ah, float al, float bh, float bl, float ch, float cl, float dh,
+                                        float dl, float& rh, float& rl) {
+  const float p1 = __fmul_rn(ah, bh);
+  const float e1 = __fmaf_rn(ah, bh, -p1);
+  const float cs = SIGN > 0 ? ch : -ch;
+  const float cls = SIGN > 0 ? cl : -cl;
+  const float p2 = __fmul_rn(cs, dh);
+  const float e2 = __fmaf_rn(cs, dh, -p2);
+  float s, es;
+  ef_two_sum(p1, p2, s, es);
+  float err = __fadd_rn(es, __fadd_rn(e1, e2));
+  err = __fmaf_rn(ah, bl, err);
+  err = __fmaf_rn(al, bh, err);
+  err = __fmaf_rn(cs, dl, err);
+  err = __fmaf_rn(cls, dh, err);
+  ef_fast_two_sum(s, err, rh, rl);
+}
+
+__device__ __forceinline__ dfc cadd(dfc a, dfc b) {
+  dfc r;
+  df_add(a.xh, a.xl, b.xh, b.xl, r.xh, r.xl);
+  df_add(a.yh, a.yl, b.yh, b.yl, r.yh, r.yl);
+  return r;
+}
+
+__device__ __forceinline__ dfc csub(dfc a, dfc b) {
+  dfc r;
+  df_add(a.xh, a.xl, -b.xh, -b.xl, r.xh, r.xl);
+  df_add(a.yh, a.yl, -b.yh, -b.yl, r.yh, r.yl);
+  return r;
+}
+
+// (x + iy)(u + iv) = (xu - yv) + i(xv + yu)
+__device__ __forceinline__ dfc cmul(dfc a, dfc b) {
+  dfc r;
+  df_dot2<-1>(a.xh, a.xl, b.xh, b.xl, a.yh, a.yl, b.yh, b.yl, r.xh, r.xl);
+  df_dot2<+1>(a.xh, a.xl, b.yh, b.yl, a.yh, a.yl, b.xh, b.xl, r.yh, r.yl);
+  return r;
+}
+
+// a * conj(b) = (xu + yv) + i(yu - xv)
+__device__ __forceinline__ dfc cmulc(dfc a, dfc b) {
+  dfc r;
+  df_dot2<+1>(a.xh, a.xl, b.xh, b.xl, a.yh, a.yl, b.yh, b.yl, r.xh, r.xl);
+  df_dot2<-1>(a.yh, a.yl, b.xh, b.xl, a.xh, a.xl, b.yh, b.yl, r.yh, r.yl);
+  return r;
+}
+
+__device__ __forceinline__ dfc mul_minus_i(dfc a) { return dfc{a.yh, a.yl, -a.xh, -a.xl}; }
+__device__ __forceinline__ dfc mul_plus_i(dfc a) { return dfc{-a.yh, -a.yl, a.xh, a.xl}; }
+
+// split of a double into hi + lo floats (round to nearest each)
+__device__ __forceinline__ void df_split(double d, float& h, float& l) {
+  h = __double2float_rn(d);
+  l = __double2float_rn(d - (double)h);
+}
+
+__host__ __device__ constexpr float df_hi(double d) { return (float)d; }
+__host__ __device__ constexpr float df_lo(double d) { return (float)(d - (double)(float)d); }
+
+// d * W16^e with double-float constants (forward W16 = exp(-2 pi i/16); inverse conjugate)
+template <bool INV>
+__device__ __forceinline__ dfc rot16(dfc d, int e) {
+  constexpr double C1 = 0.92387953251128675613, S1 = 0.38268343236508977173, C2 = 0.70710678118654752440;
+  switch (e) {
+    case 0: return d;
+    case 4: return INV ? mul_plus_i(d) : mul_minus_i(d);
+    default: {
+      double c, s;
+      switch (e) {
+        case 1: c = C1; s = S1; break;
+        case 2: c = C2; s = C2; break;
+        case 3: c = S1; s = C1; break;
+        case 5: c = -S1; s = C1; break;
+        case 6: c = -C2; s = C2; break;
+        default: c = -C1; s = S1; break;
+      }
+      // multiply by (c - i s) forward, (c + i s) inverse
+      const dfc w = INV ? dfc{df_hi(c), df_lo(c), df_hi(s), df_lo(s)} : dfc{df_hi(c), df_lo(c), df_hi(-s), df_lo(-s)};
+      return cmul(d, w);
+    }
+  }
+}
+
+}  // namespace aim

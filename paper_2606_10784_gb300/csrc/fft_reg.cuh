@@ -19,7 +19,13 @@ namespace aim {
 
 constexpr int kPadShift = 4;
 __host__ __device__ __forceinline__ int padi(int i) { return i + (i >> kPadShift); }
-__host__ __device__ __forceinline__ int padded_len(int H) { return H + (H >> kPadShift); }
+// Stride between the transforms of a CTA: the padded length plus 2, so that transforms whose
+// lanes share a warp (the W columns of a tile) start 4 (8-byte) or 2 (16-byte) banks apart.
+__host__ __device__ __forceinline__ int padded_len(int H) { return H + (H >> kPadShift) + 2; }
+
+// read-only load of a twiddle / spectrum entry
+__device__ __forceinline__ float2 ldro(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ double2 ldro(const double2* p) { return __ldg(p); }
 
 template <int R>
 __host__ __device__ constexpr int bitrev_r(int k) {
@@ -77,16 +83,43 @@ __device__ __forceinline__ void dft_reg(T2 (&v)[R]) {
   for (int k = 0; k < R; ++k) v[k] = t[k];
 }
 
-// twiddles W_{Ns R}^{k r}, r = 1..R-1, then the length-R DFT
+// twiddles W_{Ns R}^{k r}, r = 1..R-1, then the length-R DFT. Only the powers r = 1, 2, 4, 8
+// are read from the table; the others are products of at most three of them (a scattered
+// table read per power costs far more L1 wavefronts than the products cost FMAs).
 template <int LOGR, bool INV, typename T2>
 __device__ __forceinline__ void bfly(T2 (&v)[1 << LOGR], int k, int logNs, const T2* __restrict__ tw, int logP) {
   constexpr int R = 1 << LOGR;
   if (k != 0) {
     const int sh = logP - logNs - LOGR;
-#pragma unroll
-    for (int r = 1; r < R; ++r) {
-      const T2 w = __ldg(&tw[(k * r) << sh]);
-      v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+    auto app = [&](int r, const T2& w) { v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w); };
+    const T2 w1 = ldro(&tw[k << sh]);
+    app(1, w1);
+    if constexpr (R > 2) {
+      const T2 w2 = ldro(&tw[(2 * k) << sh]);
+      app(2, w2);
+      const T2 w3 = cmul(w2, w1);
+      app(3, w3);
+      if constexpr (R > 4) {
+        const T2 w4 = ldro(&tw[(4 * k) << sh]);
+        app(4, w4);
+        const T2 w5 = cmul(w4, w1);
+        app(5, w5);
+        const T2 w6 = cmul(w4, w2);
+        app(6, w6);
+        const T2 w7 = cmul(w4, w3);
+        app(7, w7);
+        if constexpr (R > 8) {
+          const T2 w8 = ldro(&tw[(8 * k) << sh]);
+          app(8, w8);
+          app(9, cmul(w8, w1));
+          app(10, cmul(w8, w2));
+          app(11, cmul(w8, w3));
+          app(12, cmul(w8, w4));
+          app(13, cmul(w8, w5));
+          app(14, cmul(w8, w6));
+          app(15, cmul(w8, w7));
+        }
+      }
     }
   }
   dft_reg<R, INV>(v);

@@ -16,22 +16,21 @@
 //   k_gather    y_i = sum over projections of coef * (P_t^T v)_i plus the near-field row
 //               (C x)_i, one warp per unknown, deterministic.
 // Each length-H transform runs as register-resident radix-16 passes (fft_reg.cuh): the first
-// pass reads its operands straight from global memory (column pass) and the last pass writes
-// straight to global memory, so shared memory carries only the exchanges between passes.
+// pass reads its operands straight from global memory (column and inverse row passes) and the
+// last pass writes straight to global memory, so shared memory carries only the exchanges
+// between passes. A thread owns TPT transforms: with TPT = 2 the even- and odd-half transforms
+// of a line sit in the same thread; with TPT = 1 they sit in adjacent lanes and recombine
+// through a lane shuffle (half the registers per thread, twice the threads). Which one is
+// faster depends on the element type; the autotuner measures both.
 // The intermediate m x P grid of a channel is stored as column tiles of W entries
 // (W * sizeof(complex) = 32 bytes) so that the column pass reads contiguous blocks and the
 // row passes touch whole 32-byte sectors. Only grid rows that hold active points are stored.
+#include <chrono>
+
 #include "aim_internal.h"
-#include "fft_reg.cuh"
+#include "gridtypes.cuh"
 
 namespace aim {
-
-template <typename T> using C2 = typename Cplx<T>::type;
-
-// threads per CTA bound: FP64 kernels hold 32 complex128 values per thread in registers
-template <typename T> struct MaxThreads;
-template <> struct MaxThreads<double> { static constexpr int value = 256; };
-template <> struct MaxThreads<float> { static constexpr int value = 512; };
 
 // ------------------------------------------------------------------------------------
 // row pass, forward
@@ -51,37 +50,42 @@ struct RowFwdArgs {
   int rows_per_cta;
 };
 
-// CTA: rows_per_cta rows of one channel; H/16 threads per row; two transforms per row (a, a w^n).
-template <typename T>
-__global__ void __launch_bounds__(MaxThreads<T>::value) k_row_fwd(RowFwdArgs a) {
-  using T2 = C2<T>;
-  constexpr int W = TileW<T>::value;
+// CTA: rows_per_cta rows of one channel; (3 - TPT) * H/16 threads per row.
+template <typename CT, int TPT>
+__global__ void __launch_bounds__(LaunchMax<CT, TPT>::value) k_row_fwd(RowFwdArgs a) {
+  using T2 = CT;
+  constexpr int W = GridT<CT>::W, NF = TPT, LPT = 3 - TPT;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
   const int H = 1 << a.logH, P = 1 << a.logP, tpf = H >> 4, HS = padded_len(H);
-  const int g = threadIdx.x / tpf, j = threadIdx.x - g * tpf;
+  const int per_row = LPT * tpf;
+  const int g = threadIdx.x / per_row, rem = threadIdx.x - g * per_row;
+  const int half = TPT == 1 ? (rem & 1) : 0, j = TPT == 1 ? (rem >> 1) : rem;
   const int rloc = blockIdx.x * a.rows_per_cta + g;
   const int c = blockIdx.y;
   const bool live = rloc < a.nrows;
   const int iy = a.row_lo + rloc;
   const T2* tw = static_cast<const T2*>(a.tw);
-  const int fb[2] = {(2 * g) * HS, (2 * g + 1) * HS};
+  const int fbA = (2 * g) * HS;
+  int fb[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) fb[f] = (2 * g + (TPT == 1 ? half : f)) * HS;
   // zero the row buffer, then anterpolate u = P_s x into it
-  for (int i = j; i < HS; i += tpf) sm[fb[0] + i] = T2{0, 0};
+  for (int i = rem; i < HS; i += per_row) sm[fbA + i] = czero<T2>();
   __syncthreads();
   if (live) {
     if (a.dense) {
       const double2* u = a.x + (size_t)c * a.m * a.m + (size_t)iy * a.m;
-      for (int ix = j; ix < a.m; ix += tpf) {
+      for (int ix = rem; ix < a.m; ix += per_row) {
         const double2 v = u[ix];
-        sm[fb[0] + padi(ix)] = T2{(T)v.x, (T)v.y};
+        sm[fbA + padi(ix)] = cfrom<T2>(v.x, v.y);
       }
     } else {
       const int pj = c / a.nrhs, r = c - pj * a.nrhs;
       const double* w = a.w[pj];
       const double2* xv = a.x + (size_t)r * a.n;
       const int a1 = a.row_ptr[iy + 1];
-      for (int ap = a.row_ptr[iy] + j; ap < a1; ap += tpf) {
+      for (int ap = a.row_ptr[iy] + rem; ap < a1; ap += per_row) {
         double re = 0.0, im = 0.0;
         const int e1 = a.sc_ptr[ap + 1];
         for (int e = a.sc_ptr[ap]; e < e1; ++e) {
@@ -90,43 +94,44 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_row_fwd(RowFwdArgs a) 
           re = fma(ww, xx.x, re);
           im = fma(ww, xx.y, im);
         }
-        sm[fb[0] + padi(a.act_ix[ap])] = T2{(T)re, (T)im};
+        sm[fbA + padi(a.act_ix[ap])] = cfrom<T2>(re, im);
       }
     }
   }
   __syncthreads();
-  // pass 0 (radix 16, Ns = 1) builds both transforms: a and a * w^n
+  // pass 0 (radix 16, Ns = 1): the transform of a and/or of a w^n
   {
     const int lognb = a.logH - 4;
-    T2 va[16], vb[16];
+    T2 v[NF][16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int nn = j + (r << lognb);
-      va[r] = sm[fb[0] + padi(nn)];
-      vb[r] = cmul(va[r], __ldg(&tw[nn]));
+      const T2 x = sm[fbA + padi(nn)];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) v[f][r] = (TPT == 1 ? half : f) ? cmul(x, ldro(&tw[nn])) : x;
     }
-    dft_reg<16, false>(va);
-    dft_reg<16, false>(vb);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) dft_reg<16, false>(v[f]);
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      sm[fb[0] + padi((j << 4) + r)] = va[r];
-      sm[fb[1] + padi((j << 4) + r)] = vb[r];
-    }
+    for (int f = 0; f < NF; ++f)
+#pragma unroll
+      for (int r = 0; r < 16; ++r) sm[fb[f] + padi((j << 4) + r)] = v[f][r];
     __syncthreads();
   }
   const int np = fft_npass(a.logH);
-  smem_passes<false, 2>(sm, fb, j, tpf, a.logH, 1, np - 1, 4, tw, a.logP, Identity{});
+  smem_passes<false, NF>(sm, fb, j, tpf, a.logH, 1, np - 1, 4, tw, a.logP, Identity{});
   int logNs = 0;
   for (int p = 0; p < np - 1; ++p) logNs += fft_logr(p, a.logH);
-  // last pass: X[2k] = A[k], X[2k+1] = B[k] straight to the tiled intermediate
+  // last pass: X[2k + half] straight to the tiled intermediate
   T2* out = static_cast<T2*>(a.inter) + (size_t)c * P * a.nrows;
-  last_pass_dispatch<false, 2>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int k, const T2 (&v)[2]) {
+  last_pass_dispatch<false, NF>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int k, const T2 (&v)[NF]) {
     if (!live) return;
-    const int q = 2 * k;
-    T2* dst = out + ((size_t)(q / W) * a.nrows + rloc) * W + (q % W);
-    dst[0] = v[0];
-    dst[1] = v[1];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const int q = 2 * k + (TPT == 1 ? half : f);
+      out[((size_t)(q / W) * a.nrows + rloc) * W + (q % W)] = v[f];
+    }
   });
 }
 
@@ -141,49 +146,64 @@ struct ColArgs {
   int tiles_per_cta;
 };
 
-// CTA: tiles_per_cta tiles of W columns of one channel; H/16 threads per column, each thread
-// owning the even- and odd-row transforms of its column. Lane order puts the W columns of a
-// row in adjacent lanes, so the global loads and stores of a warp are whole 32-byte sectors.
-template <typename T>
-__global__ void __launch_bounds__(MaxThreads<T>::value) k_col_conv(ColArgs a) {
-  using T2 = C2<T>;
-  constexpr int W = TileW<T>::value;
+// Recombination of the even- and odd-half inverse transforms: with TPT = 2 both are in the
+// thread; with TPT = 1 the partner lane holds the other one (all lanes must call this).
+template <int TPT, typename T2>
+__device__ __forceinline__ T2 recombine(const T2 (&v)[TPT], int half, const T2* __restrict__ tw, int nn) {
+  if constexpr (TPT == 2) {
+    return cadd(v[0], cmulc(v[1], ldro(&tw[nn])));
+  } else {
+    const T2 other = shfl_pair(v[0]);
+    return half ? other : cadd(v[0], cmulc(other, ldro(&tw[nn])));
+  }
+}
+
+// CTA: tiles_per_cta tiles of W columns of one channel; (3 - TPT) * H/16 threads per column.
+// Lane order puts the W columns of a row in adjacent lanes (lane pairs when TPT = 1), so the
+// global loads and stores of a warp are whole 32-byte sectors.
+template <typename CT, int TPT>
+__global__ void __launch_bounds__(LaunchMax<CT, TPT>::value) k_col_conv(ColArgs a) {
+  using T2 = CT;
+  constexpr int W = GridT<CT>::W, NF = TPT, LPT = 3 - TPT;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
   const int H = 1 << a.logH, P = 1 << a.logP, tpf = H >> 4, HS = padded_len(H);
-  const int per_tile = W * tpf;
+  const int per_tile = LPT * W * tpf;
   const int g = threadIdx.x / per_tile, rem = threadIdx.x - g * per_tile;
-  const int w = rem % W, j = rem / W;
+  const int half = TPT == 1 ? (rem & 1) : 0;
+  const int r2 = TPT == 1 ? (rem >> 1) : rem;
+  const int w = r2 % W, j = r2 / W;
   const int tile = blockIdx.x * a.tiles_per_cta + g;
   const int c = blockIdx.y;
   const int colc = g * W + w;
-  const int fb[2] = {(2 * colc) * HS, (2 * colc + 1) * HS};
+  int fb[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) fb[f] = (2 * colc + (TPT == 1 ? half : f)) * HS;
   const T2* tw = static_cast<const T2*>(a.tw);
   T2* blk = static_cast<T2*>(a.inter) + (size_t)c * P * a.nrows + (size_t)tile * a.nrows * W;
   const int row_hi = a.row_lo + a.nrows - 1;
-  // pass 0 from global: a[n] and a[n] w^n, n = j + 16-stride
+  // pass 0 from global: a[n] and/or a[n] w^n, n = j + 16-stride
   {
     const int lognb = a.logH - 4;
-    T2 va[16], vb[16];
+    T2 v[NF][16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
       const int nn = j + (r << lognb);
-      const T2 xv = (nn >= a.row_lo && nn <= row_hi) ? blk[(nn - a.row_lo) * W + w] : T2{0, 0};
-      va[r] = xv;
-      vb[r] = cmul(xv, __ldg(&tw[nn]));
-    }
-    dft_reg<16, false>(va);
-    dft_reg<16, false>(vb);
+      const T2 x = (nn >= a.row_lo && nn <= row_hi) ? blk[(nn - a.row_lo) * W + w] : czero<T2>();
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      sm[fb[0] + padi((j << 4) + r)] = va[r];
-      sm[fb[1] + padi((j << 4) + r)] = vb[r];
+      for (int f = 0; f < NF; ++f) v[f][r] = (TPT == 1 ? half : f) ? cmul(x, ldro(&tw[nn])) : x;
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      dft_reg<16, false>(v[f]);
+#pragma unroll
+      for (int r = 0; r < 16; ++r) sm[fb[f] + padi((j << 4) + r)] = v[f][r];
     }
     __syncthreads();
   }
   const int np = fft_npass(a.logH);
   // remaining forward passes; the last one multiplies by the spectrum column before storing
-  smem_passes<false, 2>(sm, fb, j, tpf, a.logH, 1, np - 1, 4, tw, a.logP, Identity{});
+  smem_passes<false, NF>(sm, fb, j, tpf, a.logH, 1, np - 1, 4, tw, a.logP, Identity{});
   int logNs = 0;
   for (int p = 0; p < np - 1; ++p) logNs += fft_logr(p, a.logH);
   {
@@ -192,21 +212,22 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_col_conv(ColArgs a) {
     const T2* col = static_cast<const T2*>(a.spec) + (size_t)qq * (H + 1);
     const int half_h = H >> 1;
     auto spec_mul = [&](int f, int k, T2 v) {
-      const T2 s = f ? __ldg(&col[half_h + 1 + min(k, H - 1 - k)]) : __ldg(&col[min(k, H - k)]);
+      const int odd = TPT == 1 ? half : f;
+      const T2 s = odd ? ldro(&col[half_h + 1 + min(k, H - 1 - k)]) : ldro(&col[min(k, H - k)]);
       return cmul(v, s);
     };
-    const int lr = fft_logr(np - 1, a.logH);
-    switch (lr) {
-      case 4: smem_pass<4, false, 2>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, spec_mul); break;
-      case 3: smem_pass<3, false, 2>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, spec_mul); break;
-      case 2: smem_pass<2, false, 2>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, spec_mul); break;
-      default: smem_pass<1, false, 2>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, spec_mul); break;
+    switch (fft_logr(np - 1, a.logH)) {
+      case 4: smem_pass<4, false, NF>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, spec_mul); break;
+      case 3: smem_pass<3, false, NF>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, spec_mul); break;
+      case 2: smem_pass<2, false, NF>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, spec_mul); break;
+      default: smem_pass<1, false, NF>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, spec_mul); break;
     }
   }
   // inverse transform; the last pass recombines y[n] = A[n] + conj(w^n) B[n] for kept rows
-  smem_passes<true, 2>(sm, fb, j, tpf, a.logH, 0, np - 1, 0, tw, a.logP, Identity{});
-  last_pass_dispatch<true, 2>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int nn, const T2 (&v)[2]) {
-    if (nn >= a.row_lo && nn <= row_hi) blk[(nn - a.row_lo) * W + w] = cadd(v[0], cmulc(v[1], __ldg(&tw[nn])));
+  smem_passes<true, NF>(sm, fb, j, tpf, a.logH, 0, np - 1, 0, tw, a.logP, Identity{});
+  last_pass_dispatch<true, NF>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int nn, const T2 (&v)[NF]) {
+    const T2 y = recombine<TPT>(v, half, tw, nn);
+    if (!half && nn >= a.row_lo && nn <= row_hi) blk[(nn - a.row_lo) * W + w] = y;
   });
 }
 
@@ -227,72 +248,69 @@ struct RowInvArgs {
   int rows_per_cta;
 };
 
-template <typename T>
-__global__ void __launch_bounds__(MaxThreads<T>::value) k_row_inv(RowInvArgs a) {
-  using T2 = C2<T>;
-  constexpr int W = TileW<T>::value;
+template <typename CT, int TPT>
+__global__ void __launch_bounds__(LaunchMax<CT, TPT>::value) k_row_inv(RowInvArgs a) {
+  using T2 = CT;
+  using VT = typename GridT<CT>::VT;
+  constexpr int W = GridT<CT>::W, NF = TPT, LPT = 3 - TPT;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
   const int H = 1 << a.logH, P = 1 << a.logP, tpf = H >> 4, HS = padded_len(H);
-  const int g = threadIdx.x / tpf, j = threadIdx.x - g * tpf;
+  const int per_row = LPT * tpf;
+  const int g = threadIdx.x / per_row, rem = threadIdx.x - g * per_row;
+  const int half = TPT == 1 ? (rem & 1) : 0, j = TPT == 1 ? (rem >> 1) : rem;
   const int rloc = blockIdx.x * a.rows_per_cta + g;
   const int c = blockIdx.y;
   const bool live = rloc < a.nrows;
   const int iy = a.row_lo + rloc;
   const T2* tw = static_cast<const T2*>(a.tw);
-  const int fb[2] = {(2 * g) * HS, (2 * g + 1) * HS};
+  const int fbA = (2 * g) * HS;
+  int fb[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) fb[f] = (2 * g + (TPT == 1 ? half : f)) * HS;
   const T2* blk = static_cast<const T2*>(a.inter) + (size_t)c * P * a.nrows;
-  // pass 0 (inverse, radix 16, Ns = 1) from global: A[k] = Y[2k], B[k] = Y[2k+1]
+  // pass 0 (inverse, radix 16, Ns = 1) from global: Y[2k] and/or Y[2k+1]
   {
     const int lognb = a.logH - 4;
-    T2 va[16], vb[16];
+    T2 v[NF][16];
 #pragma unroll
     for (int r = 0; r < 16; ++r) {
-      const int k = j + (r << lognb);
-      const int q = 2 * k;
-      if (live) {
-        const T2* src = blk + ((size_t)(q / W) * a.nrows + rloc) * W + (q % W);
-        va[r] = src[0];
-        vb[r] = src[1];
-      } else {
-        va[r] = T2{0, 0};
-        vb[r] = T2{0, 0};
+#pragma unroll
+      for (int f = 0; f < NF; ++f) {
+        const int q = 2 * (j + (r << lognb)) + (TPT == 1 ? half : f);
+        v[f][r] = live ? blk[((size_t)(q / W) * a.nrows + rloc) * W + (q % W)] : czero<T2>();
       }
     }
-    dft_reg<16, true>(va);
-    dft_reg<16, true>(vb);
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      sm[fb[0] + padi((j << 4) + r)] = va[r];
-      sm[fb[1] + padi((j << 4) + r)] = vb[r];
+    for (int f = 0; f < NF; ++f) {
+      dft_reg<16, true>(v[f]);
+#pragma unroll
+      for (int r = 0; r < 16; ++r) sm[fb[f] + padi((j << 4) + r)] = v[f][r];
     }
     __syncthreads();
   }
   const int np = fft_npass(a.logH);
-  smem_passes<true, 2>(sm, fb, j, tpf, a.logH, 1, np - 1, 4, tw, a.logP, Identity{});
+  smem_passes<true, NF>(sm, fb, j, tpf, a.logH, 1, np - 1, 4, tw, a.logP, Identity{});
   int logNs = 0;
   for (int p = 0; p < np - 1; ++p) logNs += fft_logr(p, a.logH);
-  const T sc = (T)a.scale;
+  const double sc = a.scale;
   if (a.dense) {
     double2* out = a.dense_out + (size_t)c * a.m * a.m + (size_t)iy * a.m;
-    last_pass_dispatch<true, 2>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int nn, const T2 (&v)[2]) {
-      if (live && nn < a.m) {
-        const T2 y = cadd(v[0], cmulc(v[1], __ldg(&tw[nn])));
-        out[nn] = double2{(double)(y.x * sc), (double)(y.y * sc)};
-      }
+    last_pass_dispatch<true, NF>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int nn, const T2 (&v)[NF]) {
+      const T2 y = recombine<TPT>(v, half, tw, nn);
+      if (!half && live && nn < a.m) out[nn] = cto_d2(y, sc);
     });
     return;
   }
   // sparse mode: results into registers, then through shared memory to the active points
-  constexpr int NMAX = 16;   // outputs per thread (16 per transform)
-  T2 ybuf[NMAX];
+  T2 ybuf[16];
   int ycnt = 0;
-  last_pass_dispatch<true, 2>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int nn, const T2 (&v)[2]) {
-    ybuf[ycnt++ & (NMAX - 1)] = cadd(v[0], cmulc(v[1], __ldg(&tw[nn])));
+  last_pass_dispatch<true, NF>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int nn, const T2 (&v)[NF]) {
+    ybuf[ycnt++ & 15] = recombine<TPT>(v, half, tw, nn);
   });
   __syncthreads();
-  {
-    // replay the output indices of the last pass to place the values
+  if (!half) {
+    // replay the output indices of the last pass to place the recombined values
     const int lr = fft_logr(np - 1, a.logH);
     const int R = 1 << lr, NB = 16 >> lr;
     const int nsm = (1 << logNs) - 1;
@@ -301,17 +319,14 @@ __global__ void __launch_bounds__(MaxThreads<T>::value) k_row_inv(RowInvArgs a) 
       const int b = j + t * tpf;
       const int k = b & nsm;
       const int base = ((b - k) << lr) + k;
-      for (int r = 0; r < R; ++r) sm[fb[0] + padi(base + (r << logNs))] = ybuf[q++];
+      for (int r = 0; r < R; ++r) sm[fbA + padi(base + (r << logNs))] = ybuf[q++];
     }
   }
   __syncthreads();
   if (live) {
-    T2* out = static_cast<T2*>(a.vact) + (size_t)c * a.n_act;
+    VT* out = static_cast<VT*>(a.vact) + (size_t)c * a.n_act;
     const int a1 = a.row_ptr[iy + 1];
-    for (int ap = a.row_ptr[iy] + j; ap < a1; ap += tpf) {
-      const T2 y = sm[fb[0] + padi(a.act_ix[ap])];
-      out[ap] = T2{y.x * sc, y.y * sc};
-    }
+    for (int ap = a.row_ptr[iy] + rem; ap < a1; ap += per_row) out[ap] = cto_vt(sm[fbA + padi(a.act_ix[ap])], sc);
   }
 }
 
@@ -334,9 +349,8 @@ struct GatherArgs {
   int accumulate;
 };
 
-template <typename T>
+template <typename T2>
 __global__ void k_gather(GatherArgs a) {
-  using T2 = C2<T>;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (gw >= a.n * a.nrhs) return;
@@ -417,26 +431,37 @@ static aim_status ensure_smem(K kernel, size_t bytes) {
 }
 
 size_t inter_bytes_needed(const aim_ctx* ctx, int channels, int precision) {
-  const size_t el = precision == AIM_MIXED ? sizeof(float2) : sizeof(double2);
+  const size_t el = precision == AIM_MIXED ? sizeof(float2) : sizeof(double2);   // dfc is 16 bytes too
   return (size_t)channels * ctx->P * ctx->nrows * el;
 }
 
-template <typename T>
-static aim_status launch_three_passes(aim_ctx* ctx, int channels, bool filtered, RowFwdArgs fa, RowInvArgs ia,
-                                      cudaStream_t st) {
-  using T2 = C2<T>;
-  constexpr int W = TileW<T>::value;
-  const int H = ctx->H, tpf = H / 16, HS = padded_len(H);
-  const T2* tw = std::is_same<T, double>::value ? (const T2*)ctx->tw : (const T2*)ctx->twf;
-  const void* spec;
-  if (std::is_same<T, double>::value) spec = filtered ? (const void*)ctx->specA : (const void*)ctx->specU;
-  else spec = filtered ? (const void*)ctx->specAf : (const void*)ctx->specUf;
-  if (channels > 65535) return fail(AIM_EINVAL, "too many channels in one grid pass");
-  if (H < 32) return fail(AIM_EINVAL, "embedding side P must be >= 64");
+// tables of the context in the element type of the grid product
+static const void* twiddles(const aim_ctx* c, float2*) { return c->twf; }
+static const void* twiddles(const aim_ctx* c, double2*) { return c->tw; }
+static const void* twiddles(const aim_ctx* c, dfc*) { return c->twdf; }
+static const void* spectrum(const aim_ctx* c, bool f, float2*) { return f ? (const void*)c->specAf : c->specUf; }
+static const void* spectrum(const aim_ctx* c, bool f, double2*) { return f ? (const void*)c->specA : c->specU; }
+static const void* spectrum(const aim_ctx* c, bool f, dfc*) { return f ? (const void*)c->specAdf : c->specUdf; }
+static const void* near_values(const NearField* nf, int which, float2*) { return nf->valf[which]; }
+static const void* near_values(const NearField* nf, int which, double2*) { return nf->val[which]; }
+static const void* near_values(const NearField* nf, int which, dfc*) { return nf->val[which]; }
+static int precision_of(float2*) { return AIM_MIXED; }
+static int precision_of(double2*) { return AIM_FP64_NATIVE; }
+static int precision_of(dfc*) { return AIM_FP64; }
 
-  // rows per CTA so that a CTA has at least 128 threads
+template <typename CT, int TPT>
+static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdArgs fa, RowInvArgs ia, int min_row_threads,
+                             cudaStream_t st) {
+  using T2 = CT;
+  constexpr int W = GridT<CT>::W, LPT = 3 - TPT;
+  const int H = ctx->H, tpf = H / 16, HS = padded_len(H);
+  const void* tw = twiddles(ctx, (CT*)nullptr);
+  const void* spec = spectrum(ctx, filtered, (CT*)nullptr);
+
+  // rows per CTA: at least min_row_threads threads, within the launch bound
   int rpc = 1;
-  while (rpc * tpf < 128 && rpc < ctx->nrows) rpc *= 2;
+  while (rpc * LPT * tpf < min_row_threads && rpc < ctx->nrows && 2 * rpc * LPT * tpf <= LaunchMax<CT, TPT>::value)
+    rpc *= 2;
   const int row_blocks = (ctx->nrows + rpc - 1) / rpc;
   const size_t sm_row = 2 * (size_t)rpc * HS * sizeof(T2);
 
@@ -447,17 +472,17 @@ static aim_status launch_three_passes(aim_ctx* ctx, int channels, bool filtered,
   fa.nrows = ctx->nrows;
   fa.inter = ctx->inter;
   fa.rows_per_cta = rpc;
-  AIM_TRY(ensure_smem(k_row_fwd<T>, sm_row));
+  AIM_TRY(ensure_smem(k_row_fwd<CT, TPT>, sm_row));
   {
     ProfScope ps(K_ROW_FWD, st);
-    k_row_fwd<T><<<dim3(row_blocks, channels), rpc * tpf, sm_row, st>>>(fa);
+    k_row_fwd<CT, TPT><<<dim3(row_blocks, channels), rpc * LPT * tpf, sm_row, st>>>(fa);
   }
   AIM_CUDA_TRY(cudaGetLastError());
 
   // column pass
   const int ntiles = ctx->P / W;
   int tpc = 1;
-  while (tpc * W * tpf < 128 && tpc < ntiles) tpc *= 2;
+  while (tpc * LPT * W * tpf < 128 && tpc < ntiles) tpc *= 2;
   ColArgs ca;
   ca.inter = ctx->inter;
   ca.spec = spec;
@@ -468,10 +493,10 @@ static aim_status launch_three_passes(aim_ctx* ctx, int channels, bool filtered,
   ca.nrows = ctx->nrows;
   ca.tiles_per_cta = tpc;
   const size_t sm_col = 2 * (size_t)tpc * W * HS * sizeof(T2);
-  AIM_TRY(ensure_smem(k_col_conv<T>, sm_col));
+  AIM_TRY(ensure_smem(k_col_conv<CT, TPT>, sm_col));
   {
     ProfScope ps(K_COL_CONV, st);
-    k_col_conv<T><<<dim3(ntiles / tpc, channels), tpc * W * tpf, sm_col, st>>>(ca);
+    k_col_conv<CT, TPT><<<dim3(ntiles / tpc, channels), tpc * LPT * W * tpf, sm_col, st>>>(ca);
   }
   AIM_CUDA_TRY(cudaGetLastError());
 
@@ -484,22 +509,39 @@ static aim_status launch_three_passes(aim_ctx* ctx, int channels, bool filtered,
   ia.nrows = ctx->nrows;
   ia.scale = 1.0 / ((double)ctx->P * (double)ctx->P);
   ia.rows_per_cta = rpc;
-  AIM_TRY(ensure_smem(k_row_inv<T>, sm_row));
+  AIM_TRY(ensure_smem(k_row_inv<CT, TPT>, sm_row));
   {
     ProfScope ps(K_ROW_INV, st);
-    k_row_inv<T><<<dim3(row_blocks, channels), rpc * tpf, sm_row, st>>>(ia);
+    k_row_inv<CT, TPT><<<dim3(row_blocks, channels), rpc * LPT * tpf, sm_row, st>>>(ia);
   }
   AIM_CUDA_TRY(cudaGetLastError());
   return AIM_OK;
 }
 
-template <typename T>
+template <typename CT>
+static aim_status launch_three_passes(aim_ctx* ctx, int channels, bool filtered, RowFwdArgs fa, RowInvArgs ia,
+                                      cudaStream_t st) {
+  if (channels > 65535) return fail(AIM_EINVAL, "too many channels in one grid pass");
+  if (ctx->H < 32) return fail(AIM_EINVAL, "embedding side P must be >= 64");
+  const int p = precision_of((CT*)nullptr);
+  const int tpt = ctx->sched[p].tpt;
+  const int mrt = ctx->sched[p].min_row_threads;
+  if constexpr (std::is_same<CT, double2>::value) {
+    return launch_tpt<CT, 2>(ctx, channels, filtered, fa, ia, mrt, st);
+  } else {
+    if (tpt == 1) return launch_tpt<CT, 1>(ctx, channels, filtered, fa, ia, mrt, st);
+    return launch_tpt<CT, 2>(ctx, channels, filtered, fa, ia, mrt, st);
+  }
+}
+
+template <typename CT>
 aim_status grid_pass(aim_ctx* ctx, const PassSpec& spec, int nrhs, const double2* x, double2* y,
                      cudaStream_t st) {
-  const int precision = std::is_same<T, double>::value ? AIM_FP64 : AIM_MIXED;
+  using VT = typename GridT<CT>::VT;
+  const int precision = precision_of((CT*)nullptr);
   const int channels = spec.nproj * nrhs;
   if (inter_bytes_needed(ctx, channels, precision) > ctx->inter_bytes ||
-      (size_t)channels * ctx->n_act * sizeof(C2<T>) > ctx->vact_bytes)
+      (size_t)channels * ctx->n_act * sizeof(VT) > ctx->vact_bytes)
     return fail(AIM_ESTATE, "grid workspace not reserved for this many right-hand sides");
 
   RowFwdArgs fa{};
@@ -520,7 +562,7 @@ aim_status grid_pass(aim_ctx* ctx, const PassSpec& spec, int nrhs, const double2
   ia.n_act = ctx->n_act;
   ia.row_ptr = ctx->row_ptr;
   ia.act_ix = ctx->act_ix;
-  AIM_TRY(launch_three_passes<T>(ctx, channels, spec.filtered, fa, ia, st));
+  AIM_TRY(launch_three_passes<CT>(ctx, channels, spec.filtered, fa, ia, st));
 
   GatherArgs ga{};
   ga.vact = ctx->vact;
@@ -537,8 +579,7 @@ aim_status grid_pass(aim_ctx* ctx, const PassSpec& spec, int nrhs, const double2
   if (spec.near != nullptr && spec.near->nnz > 0) {
     ga.nptr = spec.near->ptr;
     ga.ncol = spec.near->col;
-    ga.nval = std::is_same<T, double>::value ? (const void*)spec.near->val[spec.near_which]
-                                              : (const void*)spec.near->valf[spec.near_which];
+    ga.nval = near_values(spec.near, spec.near_which, (CT*)nullptr);
   }
   ga.x = x;
   ga.out_scale = spec.out_scale;
@@ -549,16 +590,16 @@ aim_status grid_pass(aim_ctx* ctx, const PassSpec& spec, int nrhs, const double2
   const long long blocks = (warps * 32 + tpb - 1) / tpb;
   {
     ProfScope ps(K_GATHER, st);
-    k_gather<T><<<(unsigned)blocks, tpb, 0, st>>>(ga);
+    k_gather<VT><<<(unsigned)blocks, tpb, 0, st>>>(ga);
   }
   AIM_CUDA_TRY(cudaGetLastError());
   return AIM_OK;
 }
 
-template <typename T>
+template <typename CT>
 aim_status grid_product_dense(aim_ctx* ctx, bool filtered, int nrhs, const double2* u, double2* v,
                               cudaStream_t st) {
-  const int precision = std::is_same<T, double>::value ? AIM_FP64 : AIM_MIXED;
+  const int precision = precision_of((CT*)nullptr);
   if (inter_bytes_needed(ctx, nrhs, precision) > ctx->inter_bytes)
     return fail(AIM_ESTATE, "grid workspace not reserved for this many grids");
   AIM_CUDA_TRY(cudaMemsetAsync(v, 0, (size_t)nrhs * ctx->m * ctx->m * sizeof(double2), st));
@@ -573,7 +614,7 @@ aim_status grid_product_dense(aim_ctx* ctx, bool filtered, int nrhs, const doubl
   ia.dense_out = v;
   ia.m = ctx->m;
   ia.n_act = ctx->n_act;
-  return launch_three_passes<T>(ctx, nrhs, filtered, fa, ia, st);
+  return launch_three_passes<CT>(ctx, nrhs, filtered, fa, ia, st);
 }
 
 aim_status gram_inv_apply(aim_ctx* ctx, int nrhs, const double2* x, double2* y, cudaStream_t st) {
@@ -589,9 +630,11 @@ aim_status gram_inv_apply(aim_ctx* ctx, int nrhs, const double2* x, double2* y, 
   return AIM_OK;
 }
 
-template aim_status grid_pass<double>(aim_ctx*, const PassSpec&, int, const double2*, double2*, cudaStream_t);
-template aim_status grid_pass<float>(aim_ctx*, const PassSpec&, int, const double2*, double2*, cudaStream_t);
-template aim_status grid_product_dense<double>(aim_ctx*, bool, int, const double2*, double2*, cudaStream_t);
-template aim_status grid_product_dense<float>(aim_ctx*, bool, int, const double2*, double2*, cudaStream_t);
+template aim_status grid_pass<double2>(aim_ctx*, const PassSpec&, int, const double2*, double2*, cudaStream_t);
+template aim_status grid_pass<float2>(aim_ctx*, const PassSpec&, int, const double2*, double2*, cudaStream_t);
+template aim_status grid_pass<dfc>(aim_ctx*, const PassSpec&, int, const double2*, double2*, cudaStream_t);
+template aim_status grid_product_dense<double2>(aim_ctx*, bool, int, const double2*, double2*, cudaStream_t);
+template aim_status grid_product_dense<float2>(aim_ctx*, bool, int, const double2*, double2*, cudaStream_t);
+template aim_status grid_product_dense<dfc>(aim_ctx*, bool, int, const double2*, double2*, cudaStream_t);
 
 }  // namespace aim

@@ -4,6 +4,7 @@
 // right-hand sides (Sec. II).
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "aim_internal.h"
 #include "fft.cuh"
@@ -110,8 +111,14 @@ __global__ void k_even_line_dft(double2* a, int H, int logP, const double2* tw, 
   for (int q = threadIdx.x; q <= H; q += blockDim.x) base[(size_t)q * stride] = sm[q];
 }
 
+__device__ __forceinline__ float4 split_df(double2 v) {
+  const float xh = __double2float_rn(v.x), yh = __double2float_rn(v.y);
+  return float4{xh, __double2float_rn(v.x - (double)xh), yh, __double2float_rn(v.y - (double)yh)};
+}
+
 __global__ void k_pack_spectrum(const double2* C, int H, int P, double eps, double alpha, int filter,
-                                double2* specU, double2* specA, float2* specUf, float2* specAf) {
+                                double2* specU, double2* specA, float2* specUf, float2* specAf, float4* specUdf,
+                                float4* specAdf) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long total = (long long)(H + 1) * (H + 1);
   if (t >= total) return;
@@ -126,6 +133,8 @@ __global__ void k_pack_spectrum(const double2* C, int H, int P, double eps, doub
   const double2 va = keep ? v : double2{0.0, 0.0};
   specA[t] = va;
   specAf[t] = float2{(float)va.x, (float)va.y};
+  specUdf[t] = split_df(v);
+  specAdf[t] = split_df(va);
 }
 
 // ------------------------------------------------------------------------------------
@@ -457,9 +466,15 @@ __global__ void k_rhs(const double2* nodes, int n, int te, double k, const doubl
 // ------------------------------------------------------------------------------------
 // host orchestration
 // ------------------------------------------------------------------------------------
+// The quadrature tables live in constant memory, one copy per device: uploaded on the first
+// setup on each device (guarded, so concurrent setups on several threads do it once).
 static aim_status upload_quad_tables() {
-  static bool done = false;
-  // per device upload (constant memory is per context); cheap, so do it every setup
+  static std::mutex mu;
+  static bool done[64] = {};
+  int dev = 0;
+  AIM_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  if (dev >= 0 && dev < 64 && done[dev]) return AIM_OK;
   QuadTables qt;
   std::vector<double> x, w;
   auto fill = [&](int nq, double* xs, double* ws) {
@@ -472,8 +487,7 @@ static aim_status upload_quad_tables() {
   fill(20, qt.x20, qt.w20);
   fill(24, qt.x24, qt.w24);
   AIM_CUDA_TRY(cudaMemcpyToSymbol(c_quad, &qt, sizeof(qt)));
-  done = true;
-  (void)done;
+  if (dev >= 0 && dev < 64) done[dev] = true;
   return AIM_OK;
 }
 
@@ -617,12 +631,15 @@ aim_status device_spectra_and_near(aim_ctx* ctx, const HostSetup& hs, cudaStream
   AIM_TRY(dev_alloc_t(ctx, &ctx->specA, nq));
   AIM_TRY(dev_alloc_t(ctx, &ctx->specUf, nq));
   AIM_TRY(dev_alloc_t(ctx, &ctx->specAf, nq));
+  AIM_TRY(dev_alloc_t(ctx, &ctx->specUdf, nq));
+  AIM_TRY(dev_alloc_t(ctx, &ctx->specAdf, nq));
   {
     const int tpb = 256;
     ProfScope ps(K_SETUP_PACK, st);
     k_pack_spectrum<<<(unsigned)((nq + tpb - 1) / tpb), tpb, 0, st>>>(samp, H, P, ctx->eps, ctx->alpha,
                                                                       ctx->filter_enabled, ctx->specU, ctx->specA,
-                                                                      ctx->specUf, ctx->specAf);
+                                                                      ctx->specUf, ctx->specAf, ctx->specUdf,
+                                                                      ctx->specAdf);
     AIM_CUDA_TRY(cudaGetLastError());
   }
   // temporaries are freed when `tmp` goes out of scope: wait for the kernels first

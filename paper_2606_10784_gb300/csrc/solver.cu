@@ -326,8 +326,8 @@ aim_status gmres_solve(aim_ctx* ctx, aim_op system, int nrhs, const double2* b, 
   std::vector<int> iters(nrhs, 0), conv(nrhs, 0), outer(nrhs, 0);
   std::vector<double> relres(nrhs, 1.0);
   aim_status st_out = AIM_OK;
-  if (opts->precision == AIM_FP64) {
-    aim_status s = gmres_core(ctx, system, AIM_FP64, nrhs, b, x, opts->tol, opts->restart, opts->max_iter, &iters,
+  if (opts->precision != AIM_MIXED) {
+    aim_status s = gmres_core(ctx, system, opts->precision, nrhs, b, x, opts->tol, opts->restart, opts->max_iter, &iters,
                               &relres, &conv, deadline, has_deadline, st);
     if (s != AIM_OK) return s;
     for (int r = 0; r < nrhs; ++r) outer[r] = 1;

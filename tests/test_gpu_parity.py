@@ -1,7 +1,8 @@
 """GPU parity: the CUDA path through the C ABI against the CPU oracle, element by element.
 
-FP64 mode: relative L2 <= 1e-10 per vector (the path computes in complex128; the gap to the
-oracle is rounding order, quadrature rules that agree to ~1e-13, and Bessel evaluations).
+FP64 modes: relative L2 <= 1e-10 per vector, both for the double-float grid arithmetic
+(precision 0, ~2^-48 per operation) and for native binary64 (precision 2); the gap to the
+oracle is rounding, quadrature rules that agree to ~1e-13, and Bessel evaluations.
 Mixed mode (complex64 grid products): relative L2 <= 1e-5 (single precision FFT of length
 P <= 4096 accumulates ~1e-6 relative error).
 """
@@ -67,7 +68,7 @@ def test_grid_product_matches_oracle(aimlib, m, P, alpha_k, radius):
         want = ref.grid_product(u, filtered)
         want[:, :inf["row_lo"], :] = 0
         want[:, inf["row_hi"] + 1:, :] = 0
-        for prec, tol in ((0, TOL64), (1, TOL32)):
+        for prec, tol in ((0, TOL64), (1, TOL32), (2, TOL64)):
             ud = dev(u)
             vd = torch.empty_like(ud)
             ctx.grid_product(ud, vd, filtered, precision=prec)
@@ -110,9 +111,10 @@ def test_te_operator_matches_oracle(te_pair, op):
          "calderon": lambda v: ref.calderon(v, filtered=False), "calderon_alpha": lambda v: ref.calderon(v, True),
          "efie": ref.N}[op]
     want = np.stack([f(v) for v in x])
-    got = run_matvec(ctx, op, x)
-    for r in range(3):
-        assert rel(got[r], want[r]) < TOL64, (op, r, rel(got[r], want[r]))
+    for prec in (0, 2):       # FP64 (double-float grid arithmetic) and native FP64
+        got = run_matvec(ctx, op, x, precision=prec)
+        for r in range(3):
+            assert rel(got[r], want[r]) < TOL64, (op, prec, r, rel(got[r], want[r]))
     if op != "gram_inv":
         got32 = run_matvec(ctx, op, x, precision=1)
         for r in range(3):
@@ -149,9 +151,10 @@ def test_tm_operator_matches_oracle(tm_pair, op):
     f = {"S": lambda v: ref.Z(v) / jk, "S_alpha": lambda v: ref.Z_alpha(v) / jk, "efie": ref.Z,
          "efie_alpha": ref.Z_alpha}[op]
     want = np.stack([f(v) for v in x])
-    got = run_matvec(ctx, op, x)
-    for r in range(2):
-        assert rel(got[r], want[r]) < TOL64, (op, r, rel(got[r], want[r]))
+    for prec in (0, 2):
+        got = run_matvec(ctx, op, x, precision=prec)
+        for r in range(2):
+            assert rel(got[r], want[r]) < TOL64, (op, prec, r, rel(got[r], want[r]))
     got32 = run_matvec(ctx, op, x, precision=1)
     for r in range(2):
         assert rel(got32[r], want[r]) < TOL32
@@ -219,7 +222,7 @@ def test_tm_circle_filtered_solve_residual_under_oracle(tm_circle):
     assert np.linalg.norm(E - ref.Z_alpha(xs)) / np.linalg.norm(E) < 1e-8
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_te_calderon_solve_matches_oracle(te_pair, precision):
     # unfiltered Calderon (well conditioned, lambda_n mu_n -> 1/4): the solutions agree
     nodes, ctx, ref = te_pair
@@ -252,3 +255,15 @@ def test_te_filtered_calderon_solve_residual_under_oracle(te_pair, precision):
     assert info[0]["converged"] == 1
     xs = x.cpu().numpy()[0]
     assert np.linalg.norm(b - ref.calderon(xs, True)) / np.linalg.norm(b) < 100 * tol
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_autotuned_schedule_gives_identical_results(te_pair, precision):
+    # every schedule does the same arithmetic in the same order: results are bit-identical
+    nodes, ctx, ref = te_pair
+    x = synth.random_coeffs(len(nodes), 2, seed=21)
+    before = run_matvec(ctx, "calderon_alpha", x, precision=precision)
+    chosen = ctx.autotune(nrhs=2, precision=precision)
+    assert chosen["transforms_per_thread"] in (1, 2)
+    after = run_matvec(ctx, "calderon_alpha", x, precision=precision)
+    assert np.array_equal(before, after)
