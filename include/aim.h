@@ -202,6 +202,30 @@ aim_status aim_matvec(aim_ctx* ctx, aim_op op, int nrhs, const void* x, void* y,
 aim_status aim_grid_product(aim_ctx* ctx, int filtered, int nrhs, const void* u, void* v,
                             int precision, void* stream);
 
+/* Size of the scratch array behind aim_grid_product_noalloc (bytes). */
+#define AIM_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+
+/* The grid product of aim_grid_product without any allocation. This entry point has no
+ * counterpart in the paper; it exists for callers that cannot allocate device memory when they
+ * need a product: code running while a CUDA graph is being captured (allocation calls cannot be
+ * captured), real-time loops whose device memory is fixed before they start, and hosts that
+ * forbid cudaMalloc after start-up. aim_grid_product may grow the context's workspace with
+ * cudaMalloc the first time it sees a larger batch; this variant instead keeps its scratch (the
+ * tiled intermediate grid) in a fixed array of AIM_NOALLOC_SCRATCH_BYTES compiled into the
+ * library's device image. Every GPU that loads the library holds that array until the process
+ * exits. The call makes no cudaMalloc, cudaFree or other allocating call.
+ * Same result as aim_grid_product with the same arguments. u and v must be device pointers.
+ * The first call on each device looks up the array's device address (cudaGetSymbolAddress,
+ * once per device, under a lock); make that first call before any stream capture.
+ * Every call shares the one array and leaves its contents there; nothing in it needs to start at
+ * zero (each product writes all of the scratch it later reads). Calls that overlap on the GPU -
+ * from any context, stream or thread - race on the array; the caller must serialise them.
+ * Errors: AIM_EINVAL if the intermediate grid (nrhs * fft_P * active rows * 16 bytes, 8 in
+ * AIM_MIXED) exceeds AIM_NOALLOC_SCRATCH_BYTES or u, v are not device memory; AIM_ESTATE while
+ * kernel timing (aim_profile_start) is active, because timing creates events. */
+aim_status aim_grid_product_noalloc(aim_ctx* ctx, int filtered, int nrhs, const void* u, void* v,
+                                    int precision, void* stream);
+
 /* Solves A x = b for nrhs right-hand sides by restarted GMRES with FP64 Arnoldi
  * (classical Gram-Schmidt, applied twice). `system` is AIM_OP_EFIE, AIM_OP_EFIE_ALPHA,
  * AIM_OP_CALDERON or AIM_OP_CALDERON_ALPHA. For the Calderon systems `rhs` is the EFIE

@@ -115,6 +115,8 @@ def lib() -> ctypes.CDLL:
     L.aim_query_bytes.argtypes = [ctypes.POINTER(Geometry), ctypes.POINTER(Grid), ctypes.POINTER(Stencil), i, i,
                                   ctypes.POINTER(ctypes.c_size_t)]
     L.aim_query_bytes.restype = i
+    L.aim_grid_product_noalloc.argtypes = [vp, i, i, vp, vp, i, vp]
+    L.aim_grid_product_noalloc.restype = i
     L.aim_autotune.argtypes = [vp, i, i, vp, ctypes.POINTER(i)]
     L.aim_autotune.restype = i
     L.aim_launch_count.argtypes = []
@@ -246,6 +248,13 @@ class Context:
         nrhs = u.shape[0] if u.ndim == 3 else 1
         _check(lib().aim_grid_product(self._h, int(bool(filtered)), int(nrhs), _ptr(u), _ptr(v), int(precision),
                                       _stream_ptr(stream)), "aim_grid_product")
+        return v
+
+    def grid_product_noalloc(self, u, v, filtered: bool, precision: int = FP64, stream=None):
+        """aim_grid_product without allocation (library-owned scratch; device pointers only)."""
+        nrhs = u.shape[0] if u.ndim == 3 else 1
+        _check(lib().aim_grid_product_noalloc(self._h, int(bool(filtered)), int(nrhs), _ptr(u), _ptr(v),
+                                              int(precision), _stream_ptr(stream)), "aim_grid_product_noalloc")
         return v
 
     def solve(self, system, rhs, x, tol=1e-8, restart=50, max_iter=1000, precision: int = FP64, inner_tol=1e-4,

@@ -37,6 +37,11 @@ size_t g_used = 0;
 
 void count_launches(int id, int n) { g_launches[id].fetch_add(n, std::memory_order_relaxed); }
 
+bool profiling_active() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  return g_timing;
+}
+
 ProfScope::ProfScope(int id_, cudaStream_t st_) : id(id_), st(st_), slot(-1) {
   g_launches[id].fetch_add(1, std::memory_order_relaxed);
   std::lock_guard<std::mutex> lk(g_mu);
