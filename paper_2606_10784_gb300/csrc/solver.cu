@@ -65,6 +65,41 @@ __global__ void k_cgs_sub(const double2* __restrict__ V, const double2* __restri
   w[t] = acc;
 }
 
+// Stage 1 of out[r][i] += sign * sum_j V[j][r][i] c[j*nrhs + r], parallel over chunks of kCgsChunk
+// Krylov vectors: part[chunk][r][i] = sum over the chunk. Stage 2 adds the chunk partial sums in
+// chunk order, so the result does not depend on scheduling.
+constexpr int kCgsChunk = 32;
+
+__global__ void k_vcombine_partial(const double2* __restrict__ V, const double2* __restrict__ c, int J, int n, int nrhs,
+                                   double2* __restrict__ part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int chunk = blockIdx.y, r = blockIdx.z;
+  if (i >= n) return;
+  const int j0 = chunk * kCgsChunk, j1 = min(J, j0 + kCgsChunk);
+  double re = 0.0, im = 0.0;
+  for (int j = j0; j < j1; ++j) {
+    const double2 v = V[((size_t)j * nrhs + r) * n + i];
+    const double2 h = c[(size_t)j * nrhs + r];
+    re += v.x * h.x - v.y * h.y;
+    im += v.x * h.y + v.y * h.x;
+  }
+  part[((size_t)chunk * nrhs + r) * n + i] = double2{re, im};
+}
+
+__global__ void k_vcombine_finish(const double2* __restrict__ part, int nchunks, int n, int nrhs, double sign,
+                                  double2* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * nrhs) return;
+  double re = 0.0, im = 0.0;
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const double2 p = part[(size_t)ch * n * nrhs + t];
+    re += p.x;
+    im += p.y;
+  }
+  out[t].x += sign * re;
+  out[t].y += sign * im;
+}
+
 __global__ void k_add_small(double2* a, const double2* b, int count) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < count) { a[t].x += b[t].x; a[t].y += b[t].y; }
@@ -133,8 +168,18 @@ aim_status dot_norms(const double2* vecs, int n, int nrhs, double2* out, cudaStr
 
 }  // namespace
 
+// out += sign * V c over J Krylov vectors (two launches, deterministic order)
+static void vcombine(const double2* V, const double2* c, int J, int n, int nrhs, double sign, double2* out,
+                     double2* part, cudaStream_t st) {
+  const int nch = (J + kCgsChunk - 1) / kCgsChunk;
+  count_launches(K_GMRES, 2);
+  k_vcombine_partial<<<dim3((n + 255) / 256, nch, nrhs), 256, 0, st>>>(V, c, J, n, nrhs, part);
+  k_vcombine_finish<<<(n * nrhs + 255) / 256, 256, 0, st>>>(part, nch, n, nrhs, sign, out);
+}
+
 static aim_status ensure_krylov(aim_ctx* ctx, int nrhs, int restart) {
-  const size_t nvec = (size_t)(restart + 1) + 3;
+  // basis (restart + 1), w, r, and the chunk partial sums of vcombine
+  const size_t nvec = (size_t)(restart + 1) + 2 + (size_t)(restart + kCgsChunk) / kCgsChunk;
   const size_t need = nvec * nrhs * ctx->n * sizeof(double2);
   if (ctx->kry_bytes < need) {
     if (ctx->kry) cudaFree(ctx->kry);
@@ -238,12 +283,12 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
     for (int j = 0; j < restart; ++j) {
       double2* Vj = ws.V + (size_t)j * vsz;
       AIM_TRY(apply_op(ctx, op, nrhs, Vj, ws.w, precision, st));
-      // CGS2 (6 launches here + 1 in dot_norms)
-      count_launches(K_GMRES, 6);
+      // CGS2 (4 launches here + 2 x 2 in vcombine + 1 in dot_norms)
+      count_launches(K_GMRES, 4);
       k_multidot<<<dim3(j + 1, nrhs), 256, 0, st>>>(ws.V, ws.w, n, nrhs, ws.dots);
-      k_cgs_sub<<<nb, tpb, 0, st>>>(ws.V, ws.dots, j + 1, n, nrhs, ws.w);
+      vcombine(ws.V, ws.dots, j + 1, n, nrhs, -1.0, ws.w, ws.tmp, st);
       k_multidot<<<dim3(j + 1, nrhs), 256, 0, st>>>(ws.V, ws.w, n, nrhs, ws.dots2);
-      k_cgs_sub<<<nb, tpb, 0, st>>>(ws.V, ws.dots2, j + 1, n, nrhs, ws.w);
+      vcombine(ws.V, ws.dots2, j + 1, n, nrhs, -1.0, ws.w, ws.tmp, st);
       k_add_small<<<blocks_for((j + 1) * nrhs, tpb), tpb, 0, st>>>(ws.dots, ws.dots2, (j + 1) * nrhs);
       AIM_TRY(dot_norms(ws.w, n, nrhs, ws.nrm, st));
       k_normalize<<<nb, tpb, 0, st>>>(ws.w, ws.nrm, ws.active, n, nrhs, ws.V + (size_t)(j + 1) * vsz);
@@ -310,8 +355,7 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
       }
     }
     AIM_CUDA_TRY(cudaMemcpyAsync(ws.dots, yv.data(), (size_t)jdone * nrhs * sizeof(double2), cudaMemcpyHostToDevice, st));
-    count_launches(K_GMRES, 1);
-    k_update_x<<<nb, tpb, 0, st>>>(ws.V, ws.dots, jdone, n, nrhs, x);
+    vcombine(ws.V, ws.dots, jdone, n, nrhs, 1.0, x, ws.tmp, st);
     AIM_CUDA_TRY(cudaGetLastError());
   }
   return AIM_OK;
