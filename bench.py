@@ -55,6 +55,11 @@ def parse():
                          "refinement; native: IEEE binary64 grid arithmetic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--workload", choices=["single", "batching", "serving"], default="single",
+                    help="single: one filtered Calderon solve per step (the default line); batching: 64 "
+                         "right-hand sides per solve (perimeter 400 wl, 1024^2 grid); serving: a Poisson "
+                         "stream of requests with p50/p99 latency")
+    ap.add_argument("--requests", type=int, default=200, help="serving: timed requests (after 10%% warm-up)")
     return ap.parse_args()
 
 
@@ -398,9 +403,102 @@ def reference_arm(args):
             "gpu_launches": 0}
 
 
+# --------------------------------------------------------------------------------------
+# batching and serving workloads (separate JSON lines; the default line is "single")
+# --------------------------------------------------------------------------------------
+def batching_arm(args):
+    """64 plane waves (angles 2 pi r/64) on one contour of perimeter 400 wl (N = 4000, 1024^2 grid),
+    all right-hand sides in every grid launch, launch schedule from the autotuner. One step = setup
+    + autotune + excitation + the batched filtered Calderon solve to 1e-5."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_10784_gb300 import aim
+    prec = {"fp64": aim.FP64, "mixed": aim.MIXED, "native": aim.FP64_NATIVE}[args.precision]
+    wl = synth.batching_scale(args.seed, nrhs=64)
+    R = len(wl.angles)
+    rhs = torch.empty((R, wl.n), dtype=torch.complex128, device="cuda")
+    x = torch.zeros_like(rhs)
+    last = {}
+
+    def step():
+        ctx = aim.Context(wl.nodes, wl.k, aim.TE, wl.m, fft_P=wl.fft_P, alpha=wl.alpha)
+        last["schedule"] = ctx.autotune(nrhs=R, precision=prec)
+        ctx.rhs_planewave(wl.angles, rhs)
+        x.zero_()
+        st, info = ctx.solve("calderon_alpha", rhs, x, tol=SOLVE_TOL, restart=RESTART, max_iter=6000, precision=prec,
+                             inner_tol=1e-4, check=False)
+        last["status"], last["info"] = st, info
+        ctx.close()
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    aim.profile_start()
+    l0 = aim.launch_count()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    prof = aim.profile_stop()
+    its = [i["iters"] for i in last["info"]]
+    return {"metric": "batched filtered Calderon solves (right-hand sides/s) at rel. residual 1e-5",
+            "value": args.steps * R / el, "unit": "rhs-solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": max(1, args.warmup), "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": "perimeter 400 wl, N=%d, grid %d^2 (P=%d), 64 plane waves, alpha=2k, GMRES(%d)"
+                                   % (wl.n, wl.m, wl.fft_P, RESTART), "schedule": last["schedule"]},
+            "solve": {"status": last["status"], "iters_min": min(its), "iters_max": max(its),
+                      "converged": sum(i["converged"] for i in last["info"])},
+            "gpu_launches": aim.launch_count() - l0,
+            "kernels": {k: {"launches": v[0], "total_ms": round(v[1], 3)} for k, v in prof.items()}}
+
+
+def serving_arm(args):
+    """Poisson stream (200 requests/s, seed 11): perimeter log-uniform in [5, 500] wavelengths at a
+    wavenumber U[pi, 4pi], N = 10 per wavelength, grid 32^2..1024^2, 1..16 plane waves, filtered
+    Calderon solves to 1e-5; admission by a device-memory budget, 4 concurrent slots."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_10784_gb300 import aim, serving
+    n_warm = max(1, args.requests // 10)
+    stream = synth.serving_stream(args.requests + n_warm, rate=200.0, seed=11)
+    reqs = []
+    for i, s in enumerate(stream):
+        nodes = synth.StarContour.from_seed(s.seed % 100000).polygon(s.perimeter, s.n_seg)
+        reqs.append(serving.SolveRequest(nodes=nodes, k=s.k, m=s.m, angles=synth.equispaced_angles(s.nrhs),
+                                         alpha=s.alpha, precision={"fp64": aim.FP64, "mixed": aim.MIXED,
+                                                                   "native": aim.FP64_NATIVE}[args.precision],
+                                         tol=SOLVE_TOL, restart=RESTART, arrival=s.t_arrival, rid=i))
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.6 * free)
+    srv = serving.Server(memory_budget_bytes=budget, slots=4)
+    serving.replay(srv, reqs[:n_warm])
+    t0 = time.perf_counter()
+    res = serving.replay(srv, reqs[n_warm:])
+    el = time.perf_counter() - t0
+    srv.close()
+    timed = [r for r in res if r.rid >= n_warm]
+    summ = serving.latency_summary(timed)
+    return {"metric": "served filtered Calderon solves: p50/p99 latency and solves/s", "value": summ.get("solves_per_s"),
+            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": args.precision, "data": "synthetic",
+            "latency": summ, "wall_s": el, "budget_bytes": budget, "refused": srv.refused,
+            "config": {"workload": "Poisson 200/s, perimeter log-U[5,500] wl, N=10/wl, grids 32^2..1024^2, "
+                                   "1..16 rhs, %d timed requests after %d warm-up" % (len(reqs) - n_warm, n_warm)}}
+
+
 def main():
     args = parse()
-    out = reference_arm(args) if args.impl == "reference" else gb300_arm(args)
+    if args.impl == "reference":
+        out = reference_arm(args)
+    elif args.workload == "batching":
+        out = batching_arm(args)
+    elif args.workload == "serving":
+        out = serving_arm(args)
+    else:
+        out = gb300_arm(args)
     if out is not None:
         print(json.dumps(out))
 

@@ -242,8 +242,11 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
   }
 
   std::vector<int> active(nrhs, 1);
-  std::vector<Zc> Hm((size_t)(restart + 1) * restart * nrhs), cs((size_t)restart * nrhs), sn((size_t)restart * nrhs),
-      g((size_t)(restart + 1) * nrhs), yv((size_t)restart * nrhs);
+  // Hessenberg columns as they are produced: column j holds rows 0..j+1 for every rhs
+  std::vector<std::vector<Zc>> Hcol;
+  Hcol.reserve(restart);
+  std::vector<Zc> cs((size_t)restart * nrhs), sn((size_t)restart * nrhs), g((size_t)(restart + 1) * nrhs),
+      yv((size_t)restart * nrhs);
   std::vector<double> beta(nrhs);
   std::vector<int> jconv(nrhs);
 
@@ -298,9 +301,11 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
       AIM_CUDA_TRY(cudaStreamSynchronize(st));
       jdone = j + 1;
       bool all_done = true;
+      if ((int)Hcol.size() <= j) Hcol.resize(j + 1);
+      Hcol[j].assign((size_t)(j + 2) * nrhs, Zc{0.0, 0.0});
+      Zc* col = Hcol[j].data();   // column j, rows 0..j+1
       for (int r = 0; r < nrhs; ++r) {
         if (!active[r] || jconv[r]) continue;
-        Zc* col = &Hm[((size_t)j * (restart + 1)) * nrhs];   // column j, rows 0..j+1
         for (int i = 0; i <= j; ++i) col[(size_t)i * nrhs + r] = {hred[(size_t)i * nrhs + r].x, hred[(size_t)i * nrhs + r].y};
         const double hn = std::sqrt(std::fmax(hred[(size_t)(j + 1) * nrhs + r].x, 0.0));
         if (!std::isfinite(hn)) return fail(AIM_ENUMERIC, "non-finite Arnoldi norm");
@@ -344,11 +349,11 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
       for (int i = J - 1; i >= 0; --i) {
         Zc acc = g[(size_t)i * nrhs + r];
         for (int l = i + 1; l < J; ++l) {
-          const Zc t = cm(Hm[((size_t)l * (restart + 1) + i) * nrhs + r], yv[(size_t)l * nrhs + r]);
+          const Zc t = cm(Hcol[l][(size_t)i * nrhs + r], yv[(size_t)l * nrhs + r]);
           acc.re -= t.re;
           acc.im -= t.im;
         }
-        const Zc d = Hm[((size_t)i * (restart + 1) + i) * nrhs + r];
+        const Zc d = Hcol[i][(size_t)i * nrhs + r];
         const double dd = cabs2(d);
         yv[(size_t)i * nrhs + r] = dd > 0 ? Zc{(acc.re * d.re + acc.im * d.im) / dd, (acc.im * d.re - acc.re * d.im) / dd}
                                           : Zc{0.0, 0.0};
