@@ -125,7 +125,9 @@ typedef struct {
   int max_iter;        /* total inner iterations per right-hand side */
   int precision;       /* AIM_FP64, AIM_FP64_NATIVE, or AIM_MIXED (FP32 grid inner solves inside
                           iterative refinement with AIM_FP64 residuals) */
-  double inner_tol;    /* mixed only: relative tolerance of each inner FP32-grid solve (e.g. 1e-4) */
+  double inner_tol;    /* mixed only: relative tolerance of each inner FP32-grid solve; <= 0 asks for
+                          just the remaining reduction, 0.9 tol ||b|| / ||r||, but at least 1e-5
+                          (the complex64 product's noise floor on nearly singular systems) */
   int timeout_ms;      /* <= 0: no limit */
 } aim_solve_opts;
 
@@ -171,13 +173,30 @@ aim_status aim_get_info(const aim_ctx* ctx, aim_info* info);
  * so that later calls (and CUDA-graph capture of them) allocate nothing. */
 aim_status aim_reserve(aim_ctx* ctx, int nrhs, int precision);
 
+/* Launch schedule of the three grid kernels for one precision (no counterpart in the
+ * paper). transforms_per_thread: 1 puts the even- and odd-half transforms of a line in
+ * adjacent lanes, 2 puts both in one thread (native FP64 allows 2 only). row_threads: the
+ * least threads of a row-pass CTA (32..1024; rows are added to a CTA until it has that many).
+ * col_cols: columns of one column-pass CTA, a power of two, 0 for the default (the fewest
+ * whole 32-byte column tiles that give 128 threads). Results are identical under every
+ * schedule: the arithmetic and its order do not depend on it. */
+typedef struct {
+  int transforms_per_thread;
+  int row_threads;
+  int col_cols;
+} aim_schedule;
+
+/* Sets the schedule of `precision` for this context. AIM_EINVAL when it cannot be launched
+ * for the context's transform length (launch bound or 227 KB shared-memory limit). */
+aim_status aim_set_schedule(aim_ctx* ctx, int precision, const aim_schedule* schedule);
+aim_status aim_get_schedule(const aim_ctx* ctx, int precision, aim_schedule* schedule);
+
 /* Autotuner (no counterpart in the paper; a launch-schedule choice). Times the filtered
- * product (S^alpha) for nrhs vectors under each candidate schedule of the grid kernels -
- * one or two transforms per thread, 128 or 256 threads per row-pass CTA - and keeps the
- * fastest for this context and precision. Results are identical under every schedule
- * (same arithmetic, same order). Synchronises `stream`. *chosen (host, may be NULL)
- * receives tpt * 1000 + row threads of the winner. */
-aim_status aim_autotune(aim_ctx* ctx, int nrhs, int precision, void* stream, int* chosen);
+ * product (S^alpha) for nrhs vectors under each feasible schedule - one or two transforms
+ * per thread, 128 or 256 row-pass threads, and 1 to 8 columns per column-pass CTA - and
+ * keeps the fastest for this context and precision. Synchronises `stream`. *chosen (host,
+ * may be NULL) receives the winner. */
+aim_status aim_autotune(aim_ctx* ctx, int nrhs, int precision, void* stream, aim_schedule* chosen);
 
 /* Right-hand sides for unit plane waves exp(-j k khat.r), khat = (cos th, sin th):
  * TE: E_i = <phi_i, (jk/eta) E_t> with E^i = eta H^i_z (z x khat) (Sec. II, below Eq. 2);

@@ -61,6 +61,14 @@ class Info(ctypes.Structure):
                 ("setup_seconds", ctypes.c_double)]
 
 
+class Schedule(ctypes.Structure):
+    _fields_ = [("transforms_per_thread", ctypes.c_int), ("row_threads", ctypes.c_int), ("col_cols", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        return {"transforms_per_thread": self.transforms_per_thread, "row_threads": self.row_threads,
+                "col_cols": self.col_cols}
+
+
 class KernelStat(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int), ("name", ctypes.c_char_p), ("launches", ctypes.c_longlong),
                 ("total_ms", ctypes.c_double)]
@@ -117,8 +125,12 @@ def lib() -> ctypes.CDLL:
     L.aim_query_bytes.restype = i
     L.aim_grid_product_noalloc.argtypes = [vp, i, i, vp, vp, i, vp]
     L.aim_grid_product_noalloc.restype = i
-    L.aim_autotune.argtypes = [vp, i, i, vp, ctypes.POINTER(i)]
+    L.aim_autotune.argtypes = [vp, i, i, vp, ctypes.POINTER(Schedule)]
     L.aim_autotune.restype = i
+    L.aim_set_schedule.argtypes = [vp, i, ctypes.POINTER(Schedule)]
+    L.aim_set_schedule.restype = i
+    L.aim_get_schedule.argtypes = [vp, i, ctypes.POINTER(Schedule)]
+    L.aim_get_schedule.restype = i
     L.aim_launch_count.argtypes = []
     L.aim_launch_count.restype = ctypes.c_longlong
     L.aim_profile_start.argtypes = []
@@ -226,10 +238,19 @@ class Context:
 
     def autotune(self, nrhs: int = 1, precision: int = FP64, stream=None) -> dict:
         """Pick the fastest launch schedule for this context; returns it."""
-        chosen = ctypes.c_int(0)
+        chosen = Schedule()
         _check(lib().aim_autotune(self._h, int(nrhs), int(precision), _stream_ptr(stream), ctypes.byref(chosen)),
                "aim_autotune")
-        return {"transforms_per_thread": chosen.value // 1000, "min_row_threads": chosen.value % 1000}
+        return chosen.as_dict()
+
+    def set_schedule(self, precision: int, transforms_per_thread: int, row_threads: int, col_cols: int = 0):
+        sc = Schedule(int(transforms_per_thread), int(row_threads), int(col_cols))
+        _check(lib().aim_set_schedule(self._h, int(precision), ctypes.byref(sc)), "aim_set_schedule")
+
+    def get_schedule(self, precision: int) -> dict:
+        sc = Schedule()
+        _check(lib().aim_get_schedule(self._h, int(precision), ctypes.byref(sc)), "aim_get_schedule")
+        return sc.as_dict()
 
     def rhs_planewave(self, angles, out, stream=None):
         ang = np.ascontiguousarray(np.asarray(angles, dtype=np.float64).reshape(-1))
@@ -257,7 +278,7 @@ class Context:
                                               int(precision), _stream_ptr(stream)), "aim_grid_product_noalloc")
         return v
 
-    def solve(self, system, rhs, x, tol=1e-8, restart=50, max_iter=1000, precision: int = FP64, inner_tol=1e-4,
+    def solve(self, system, rhs, x, tol=1e-8, restart=50, max_iter=1000, precision: int = FP64, inner_tol=0.0,
               timeout_ms=0, x0_given=False, stream=None, check=True):
         system = OPS[system] if isinstance(system, str) else int(system)
         nrhs = rhs.shape[0] if rhs.ndim == 2 else 1

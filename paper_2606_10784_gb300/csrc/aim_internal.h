@@ -95,11 +95,17 @@ struct NearField {
 };
 
 // Launch schedule of the grid kernels for one precision: transforms per thread (1: even/odd
-// halves in adjacent lanes, 2: both in one thread) and the minimum threads of a row-pass CTA.
+// halves in adjacent lanes, 2: both in one thread), the minimum threads of a row-pass CTA, and
+// the columns of a column-pass CTA (0: the fewest whole tiles that give 128 threads).
 struct Schedule {
   int tpt;
   int min_row_threads;
+  int col_cols;
 };
+
+// Whether a schedule can be launched for a context whose transforms have length H = 2^logH
+// (checks the launch bounds and the shared-memory limit; precision selects the element type).
+bool schedule_feasible(int precision, int logH, int logP, const Schedule& s);
 
 // operator selection for one batched grid pass
 struct PassSpec {
@@ -153,7 +159,7 @@ struct aim_ctx {
   double* red_host = nullptr; size_t red_host_bytes = 0;
   int reserved_rhs[3] = {0, 0, 0};   // per precision (AIM_FP64, AIM_MIXED, AIM_FP64_NATIVE)
   // launch schedule per precision; defaults measured on GB300, aim_autotune re-measures
-  aim::Schedule sched[3] = {{1, 128}, {2, 128}, {2, 128}};
+  aim::Schedule sched[3] = {{1, 128, 0}, {2, 128, 0}, {2, 128, 0}};
   // bookkeeping
   std::vector<void*> allocations;
   size_t device_bytes = 0;

@@ -347,7 +347,25 @@ aim_status aim_reserve(aim_ctx* ctx, int nrhs, int precision) {
   return reserve(ctx, nrhs, precision);
 }
 
-aim_status aim_autotune(aim_ctx* ctx, int nrhs, int precision, void* stream, int* chosen) {
+aim_status aim_set_schedule(aim_ctx* ctx, int precision, const aim_schedule* schedule) {
+  if (!ctx || !schedule) return fail(AIM_EINVAL, "bad argument");
+  if (precision < AIM_FP64 || precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "precision must be 0, 1 or 2");
+  const Schedule sc{schedule->transforms_per_thread, schedule->row_threads, schedule->col_cols};
+  if (!schedule_feasible(precision, ctx->logH, ctx->logP, sc))
+    return fail(AIM_EINVAL, "schedule cannot be launched for this transform length");
+  ctx->sched[precision] = sc;
+  return AIM_OK;
+}
+
+aim_status aim_get_schedule(const aim_ctx* ctx, int precision, aim_schedule* schedule) {
+  if (!ctx || !schedule) return fail(AIM_EINVAL, "bad argument");
+  if (precision < AIM_FP64 || precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "precision must be 0, 1 or 2");
+  const Schedule& sc = ctx->sched[precision];
+  *schedule = aim_schedule{sc.tpt, sc.min_row_threads, sc.col_cols};
+  return AIM_OK;
+}
+
+aim_status aim_autotune(aim_ctx* ctx, int nrhs, int precision, void* stream, aim_schedule* chosen) {
   if (!ctx || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
   if (precision < AIM_FP64 || precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "precision must be 0, 1 or 2");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -363,30 +381,35 @@ aim_status aim_autotune(aim_ctx* ctx, int nrhs, int precision, void* stream, int
   float best_ms = 1e30f;
   const int tpts[2] = {1, 2};
   const int rows[2] = {128, 256};
+  const int cols[5] = {0, 1, 2, 4, 8};
   aim_status s = AIM_OK;
-  for (int a = 0; a < 2 && s == AIM_OK; ++a) {
-    if (precision == AIM_FP64_NATIVE && tpts[a] == 1) continue;   // native FP64 keeps two per thread
-    for (int b = 0; b < 2 && s == AIM_OK; ++b) {
-      ctx->sched[precision] = Schedule{tpts[a], rows[b]};
-      s = apply_op(ctx, AIM_OP_S_ALPHA, nrhs, ctx->stage_in, ctx->stage_out, precision, st);   // warm
-      if (s != AIM_OK) break;
-      cudaEventRecord(e0, st);
-      for (int it = 0; it < 3 && s == AIM_OK; ++it)
-        s = apply_op(ctx, AIM_OP_S_ALPHA, nrhs, ctx->stage_in, ctx->stage_out, precision, st);
-      cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess) { s = fail(AIM_ECUDA, "autotune event"); break; }
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (ms < best_ms) {
-        best_ms = ms;
-        best = ctx->sched[precision];
+  for (int a = 0; a < 2 && s == AIM_OK; ++a)
+    for (int b = 0; b < 2 && s == AIM_OK; ++b)
+      for (int cc = 0; cc < 5 && s == AIM_OK; ++cc) {
+        const Schedule cand{tpts[a], rows[b], cols[cc]};
+        if (!schedule_feasible(precision, ctx->logH, ctx->logP, cand)) continue;
+        ctx->sched[precision] = cand;
+        s = apply_op(ctx, AIM_OP_S_ALPHA, nrhs, ctx->stage_in, ctx->stage_out, precision, st);   // warm
+        if (s != AIM_OK) break;
+        cudaEventRecord(e0, st);
+        for (int it = 0; it < 3 && s == AIM_OK; ++it)
+          s = apply_op(ctx, AIM_OP_S_ALPHA, nrhs, ctx->stage_in, ctx->stage_out, precision, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { s = fail(AIM_ECUDA, "autotune event"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+          best_ms = ms;
+          best = cand;
+        }
       }
-    }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   ctx->sched[precision] = s == AIM_OK ? best : saved;
-  if (chosen) *chosen = ctx->sched[precision].tpt * 1000 + ctx->sched[precision].min_row_threads;
+  if (chosen) {
+    const Schedule& w = ctx->sched[precision];
+    *chosen = aim_schedule{w.tpt, w.min_row_threads, w.col_cols};
+  }
   return s;
 }
 

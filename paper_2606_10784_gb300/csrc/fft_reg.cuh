@@ -83,41 +83,53 @@ __device__ __forceinline__ void dft_reg(T2 (&v)[R]) {
   for (int k = 0; k < R; ++k) v[k] = t[k];
 }
 
-// twiddles W_{Ns R}^{k r}, r = 1..R-1, then the length-R DFT. Only the powers r = 1, 2, 4, 8
-// are read from the table; the others are products of at most three of them (a scattered
-// table read per power costs far more L1 wavefronts than the products cost FMAs).
+// Where the twiddles of a pass come from. Complex64: only the powers r = 1, 2, 4, 8 are read
+// from the table and the others are products of at most three of them (a scattered table read
+// per power costs more L1 wavefronts than the products cost FMAs, and the complex64 passes keep
+// L1 busy). Types whose complex product costs tens of FP32-pipe instructions (double-float) or
+// runs on the slow FP64 pipe (binary64) read every factor from the table instead.
+template <typename T2> struct TwiddleFromTable { static constexpr bool value = false; };
+template <> struct TwiddleFromTable<double2> { static constexpr bool value = true; };
+
+// twiddles W_{Ns R}^{k r}, r = 1..R-1, then the length-R DFT.
 template <int LOGR, bool INV, typename T2>
 __device__ __forceinline__ void bfly(T2 (&v)[1 << LOGR], int k, int logNs, const T2* __restrict__ tw, int logP) {
   constexpr int R = 1 << LOGR;
   if (k != 0) {
     const int sh = logP - logNs - LOGR;
     auto app = [&](int r, const T2& w) { v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w); };
-    const T2 w1 = ldro(&tw[k << sh]);
-    app(1, w1);
-    if constexpr (R > 2) {
-      const T2 w2 = ldro(&tw[(2 * k) << sh]);
-      app(2, w2);
-      const T2 w3 = cmul(w2, w1);
-      app(3, w3);
-      if constexpr (R > 4) {
-        const T2 w4 = ldro(&tw[(4 * k) << sh]);
-        app(4, w4);
-        const T2 w5 = cmul(w4, w1);
-        app(5, w5);
-        const T2 w6 = cmul(w4, w2);
-        app(6, w6);
-        const T2 w7 = cmul(w4, w3);
-        app(7, w7);
-        if constexpr (R > 8) {
-          const T2 w8 = ldro(&tw[(8 * k) << sh]);
-          app(8, w8);
-          app(9, cmul(w8, w1));
-          app(10, cmul(w8, w2));
-          app(11, cmul(w8, w3));
-          app(12, cmul(w8, w4));
-          app(13, cmul(w8, w5));
-          app(14, cmul(w8, w6));
-          app(15, cmul(w8, w7));
+    if constexpr (TwiddleFromTable<T2>::value) {
+      // (r k) << sh < R Ns 2^sh = P: inside the table
+#pragma unroll
+      for (int r = 1; r < R; ++r) app(r, ldro(&tw[(r * k) << sh]));
+    } else {
+      const T2 w1 = ldro(&tw[k << sh]);
+      app(1, w1);
+      if constexpr (R > 2) {
+        const T2 w2 = ldro(&tw[(2 * k) << sh]);
+        app(2, w2);
+        const T2 w3 = cmul(w2, w1);
+        app(3, w3);
+        if constexpr (R > 4) {
+          const T2 w4 = ldro(&tw[(4 * k) << sh]);
+          app(4, w4);
+          const T2 w5 = cmul(w4, w1);
+          app(5, w5);
+          const T2 w6 = cmul(w4, w2);
+          app(6, w6);
+          const T2 w7 = cmul(w4, w3);
+          app(7, w7);
+          if constexpr (R > 8) {
+            const T2 w8 = ldro(&tw[(8 * k) << sh]);
+            app(8, w8);
+            app(9, cmul(w8, w1));
+            app(10, cmul(w8, w2));
+            app(11, cmul(w8, w3));
+            app(12, cmul(w8, w4));
+            app(13, cmul(w8, w5));
+            app(14, cmul(w8, w6));
+            app(15, cmul(w8, w7));
+          }
         }
       }
     }
@@ -220,6 +232,43 @@ __device__ __forceinline__ void last_pass_dispatch(const T2* sm, const int (&fb)
     case 2: last_pass<2, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, emit); break;
     default: last_pass<1, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, emit); break;
   }
+}
+
+// The middle of a convolution: the last forward pass, the pointwise product, and the first
+// pass of the inverse transform, in registers. The last Stockham pass (Ns = H/R) of butterfly b
+// writes the outputs X[b + r H/R], which are exactly the inputs of butterfly b of an inverse
+// pass with the same radix R and Ns = 1. So when the inverse runs its radices in the reverse
+// order (R first, then the radix-16 passes), nothing goes through shared memory between the
+// two. `mul(f, k, value)` multiplies forward output k of transform f. The inverse pass writes
+// its outputs (index b R + r) to shared memory: barrier before and after the stores.
+template <int LOGR, int NF, typename T2, typename Mul>
+__device__ __forceinline__ void conv_mid_pass(T2* __restrict__ sm, const int (&fb)[NF], int j, int tpf, int logH,
+                                              const T2* __restrict__ tw, int logP, Mul mul) {
+  constexpr int R = 1 << LOGR, NB = 16 >> LOGR;
+  const int lognb = logH - LOGR;
+  T2 v[NF][NB][R];
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const int b = j + t * tpf;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[f][t][r] = sm[fb[f] + padi(b + (r << lognb))];
+      bfly<LOGR, false>(v[f][t], b, lognb, tw, logP);   // Ns = H/R, so b mod Ns = b
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[f][t][r] = mul(f, b + (r << lognb), v[f][t][r]);
+      dft_reg<R, true>(v[f][t]);                         // inverse pass with Ns = 1: no twiddles
+    }
+  __syncthreads();
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int t = 0; t < NB; ++t) {
+      const int b = j + t * tpf;
+#pragma unroll
+      for (int r = 0; r < R; ++r) sm[fb[f] + padi((b << LOGR) + r)] = v[f][t][r];
+    }
+  __syncthreads();
 }
 
 struct Identity {

@@ -26,6 +26,9 @@ template <> struct GridT<dfc> {
   using VT = double2;
   static constexpr int W = 2, MaxThreads = 512;
 };
+// a double-float complex product is ~40 FP32-pipe instructions: twiddles come whole from the table
+template <> struct TwiddleFromTable<dfc> { static constexpr bool value = true; };
+
 template <typename CT, int TPT> struct LaunchMax {
   static constexpr int value = TPT == 1 ? GridT<CT>::MaxThreads : GridT<CT>::MaxThreads / 2;
 };

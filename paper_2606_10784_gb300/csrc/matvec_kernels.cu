@@ -143,7 +143,7 @@ struct ColArgs {
   const void* spec;
   const void* tw;
   int logH, logP, row_lo, nrows;
-  int tiles_per_cta;
+  int log_cols;        // log2 of the columns of one channel per CTA
 };
 
 // Recombination of the even- and odd-half inverse transforms: with TPT = 2 both are in the
@@ -158,9 +158,11 @@ __device__ __forceinline__ T2 recombine(const T2 (&v)[TPT], int half, const T2* 
   }
 }
 
-// CTA: tiles_per_cta tiles of W columns of one channel; (3 - TPT) * H/16 threads per column.
-// Lane order puts the W columns of a row in adjacent lanes (lane pairs when TPT = 1), so the
-// global loads and stores of a warp are whole 32-byte sectors.
+// CTA: 2^log_cols consecutive columns of one channel; (3 - TPT) * H/16 threads per column.
+// Lane order puts the columns of a tile that the CTA holds (min(2^log_cols, W) of them) in
+// adjacent lanes (lane pairs when TPT = 1), so with a whole tile per CTA the global loads and
+// stores of a warp are whole 32-byte sectors; with fewer columns per CTA the CTAs of the
+// neighbouring columns read the rest of each sector, through L2.
 template <typename CT, int TPT>
 __global__ void __launch_bounds__(LaunchMax<CT, TPT>::value) k_col_conv(ColArgs a) {
   using T2 = CT;
@@ -168,14 +170,16 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT>::value) k_col_conv(ColArgs 
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
   const int H = 1 << a.logH, P = 1 << a.logP, tpf = H >> 4, HS = padded_len(H);
-  const int per_tile = LPT * W * tpf;
-  const int g = threadIdx.x / per_tile, rem = threadIdx.x - g * per_tile;
+  const int cw = min(1 << a.log_cols, W);               // columns side by side in the lanes
+  const int per_grp = LPT * cw * tpf;
+  const int g = threadIdx.x / per_grp, rem = threadIdx.x - g * per_grp;
   const int half = TPT == 1 ? (rem & 1) : 0;
   const int r2 = TPT == 1 ? (rem >> 1) : rem;
-  const int w = r2 % W, j = r2 / W;
-  const int tile = blockIdx.x * a.tiles_per_cta + g;
+  const int wl = r2 & (cw - 1), j = r2 / cw;
+  const int colc = g * cw + wl;                         // column within the CTA
+  const int qcol = (blockIdx.x << a.log_cols) + colc;   // column of the grid
+  const int w = qcol & (W - 1), tile = qcol / W;
   const int c = blockIdx.y;
-  const int colc = g * W + w;
   int fb[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) fb[f] = (2 * colc + (TPT == 1 ? half : f)) * HS;
@@ -202,13 +206,13 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT>::value) k_col_conv(ColArgs 
     __syncthreads();
   }
   const int np = fft_npass(a.logH);
-  // remaining forward passes; the last one multiplies by the spectrum column before storing
+  // remaining forward passes but the last
   smem_passes<false, NF>(sm, fb, j, tpf, a.logH, 1, np - 1, 4, tw, a.logP, Identity{});
-  int logNs = 0;
-  for (int p = 0; p < np - 1; ++p) logNs += fft_logr(p, a.logH);
+  // last forward pass, product with the spectrum column, first inverse pass (same radix), in
+  // registers; the inverse then runs its radix-16 passes
+  const int lr0 = fft_logr(np - 1, a.logH);
   {
-    const int q = tile * W + w;
-    const int qq = min(q, P - q);
+    const int qq = min(qcol, P - qcol);
     const T2* col = static_cast<const T2*>(a.spec) + (size_t)qq * (H + 1);
     const int half_h = H >> 1;
     auto spec_mul = [&](int f, int k, T2 v) {
@@ -216,16 +220,17 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT>::value) k_col_conv(ColArgs 
       const T2 s = odd ? ldro(&col[half_h + 1 + min(k, H - 1 - k)]) : ldro(&col[min(k, H - k)]);
       return cmul(v, s);
     };
-    switch (fft_logr(np - 1, a.logH)) {
-      case 4: smem_pass<4, false, NF>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, spec_mul); break;
-      case 3: smem_pass<3, false, NF>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, spec_mul); break;
-      case 2: smem_pass<2, false, NF>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, spec_mul); break;
-      default: smem_pass<1, false, NF>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, spec_mul); break;
+    switch (lr0) {
+      case 4: conv_mid_pass<4, NF>(sm, fb, j, tpf, a.logH, tw, a.logP, spec_mul); break;
+      case 3: conv_mid_pass<3, NF>(sm, fb, j, tpf, a.logH, tw, a.logP, spec_mul); break;
+      case 2: conv_mid_pass<2, NF>(sm, fb, j, tpf, a.logH, tw, a.logP, spec_mul); break;
+      default: conv_mid_pass<1, NF>(sm, fb, j, tpf, a.logH, tw, a.logP, spec_mul); break;
     }
   }
-  // inverse transform; the last pass recombines y[n] = A[n] + conj(w^n) B[n] for kept rows
-  smem_passes<true, NF>(sm, fb, j, tpf, a.logH, 0, np - 1, 0, tw, a.logP, Identity{});
-  last_pass_dispatch<true, NF>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int nn, const T2 (&v)[NF]) {
+  for (int p = 1; p < np - 1; ++p)
+    smem_pass<4, true, NF>(sm, fb, j, tpf, a.logH, lr0 + 4 * (p - 1), tw, a.logP, Identity{});
+  // last inverse pass (radix 16, Ns = H/16) recombines y[n] = A[n] + conj(w^n) B[n] for kept rows
+  last_pass<4, true, NF>(sm, fb, j, tpf, a.logH, a.logH - 4, tw, a.logP, [&](int nn, const T2 (&v)[NF]) {
     const T2 y = recombine<TPT>(v, half, tw, nn);
     if (!half && nn >= a.row_lo && nn <= row_hi) blk[(nn - a.row_lo) * W + w] = y;
   });
@@ -349,47 +354,81 @@ struct GatherArgs {
   int accumulate;
 };
 
-template <typename T2>
+// One warp per unknown i and block of up to kGatherRhs right-hand sides (1 when there is only
+// one): the CSR entries of row i (weights, active-point indices, near-field values and columns)
+// are loaded once and used for every right-hand side of the block. For each right-hand side the
+// lanes sum the entries e = lane, lane + 32, ... in order and then reduce by shuffles, so the
+// result does not depend on the block size.
+template <typename T2, int kGatherRhs>
 __global__ void k_gather(GatherArgs a) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (gw >= a.n * a.nrhs) return;
-  const int r = gw / a.n, i = gw - r * a.n;
-  double re = 0.0, im = 0.0;
+  const int nblk = (a.nrhs + kGatherRhs - 1) / kGatherRhs;
+  if (gw >= a.n * nblk) return;
+  const int rb = gw / a.n, i = gw - rb * a.n;
+  const int r0 = rb * kGatherRhs, nr = min(kGatherRhs, a.nrhs - r0);
+  double re[kGatherRhs], im[kGatherRhs];
+#pragma unroll
+  for (int q = 0; q < kGatherRhs; ++q) re[q] = im[q] = 0.0;
   const int e0 = a.ga_ptr[i], e1 = a.ga_ptr[i + 1];
   for (int pj = 0; pj < a.nproj; ++pj) {
-    const T2* v = static_cast<const T2*>(a.vact) + (size_t)(pj * a.nrhs + r) * a.n_act;
+    const T2* v = static_cast<const T2*>(a.vact) + (size_t)(pj * a.nrhs + r0) * a.n_act;
     const double* w = a.w[pj];
-    double cr = 0.0, ci = 0.0;
+    double cr[kGatherRhs], ci[kGatherRhs];
+#pragma unroll
+    for (int q = 0; q < kGatherRhs; ++q) cr[q] = ci[q] = 0.0;
     for (int e = e0 + lane; e < e1; e += 32) {
       const double ww = w[e];
-      const T2 val = v[a.ga_act[e]];
-      cr = fma(ww, (double)val.x, cr);
-      ci = fma(ww, (double)val.y, ci);
+      const int act = a.ga_act[e];
+#pragma unroll
+      for (int q = 0; q < kGatherRhs; ++q) {
+        if (q < nr) {
+          const T2 val = v[(size_t)q * a.n_act + act];
+          cr[q] = fma(ww, (double)val.x, cr[q]);
+          ci[q] = fma(ww, (double)val.y, ci[q]);
+        }
+      }
     }
-    re += a.coef[pj].x * cr - a.coef[pj].y * ci;
-    im += a.coef[pj].x * ci + a.coef[pj].y * cr;
+    const double2 cf = a.coef[pj];
+#pragma unroll
+    for (int q = 0; q < kGatherRhs; ++q) {
+      re[q] += cf.x * cr[q] - cf.y * ci[q];
+      im[q] += cf.x * ci[q] + cf.y * cr[q];
+    }
   }
   if (a.nptr != nullptr) {
     const T2* val = static_cast<const T2*>(a.nval);
-    const double2* xv = a.x + (size_t)r * a.n;
     const int n1 = a.nptr[i + 1];
     for (int e = a.nptr[i] + lane; e < n1; e += 32) {
       const T2 cv = val[e];
-      const double2 xx = xv[a.ncol[e]];
-      re += (double)cv.x * xx.x - (double)cv.y * xx.y;
-      im += (double)cv.x * xx.y + (double)cv.y * xx.x;
+      const int col = a.ncol[e];
+#pragma unroll
+      for (int q = 0; q < kGatherRhs; ++q) {
+        if (q < nr) {
+          const double2 xx = a.x[(size_t)(r0 + q) * a.n + col];
+          re[q] += (double)cv.x * xx.x - (double)cv.y * xx.y;
+          im[q] += (double)cv.x * xx.y + (double)cv.y * xx.x;
+        }
+      }
     }
   }
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    re += __shfl_xor_sync(0xffffffffu, re, off);
-    im += __shfl_xor_sync(0xffffffffu, im, off);
+  for (int q = 0; q < kGatherRhs; ++q) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      re[q] += __shfl_xor_sync(0xffffffffu, re[q], off);
+      im[q] += __shfl_xor_sync(0xffffffffu, im[q], off);
+    }
   }
-  if (lane == 0) {
+  if (lane < nr) {
+    // lane q writes right-hand side r0 + q (select by unrolled compare: no local-memory indexing)
+    double xr = 0.0, xi = 0.0;
+#pragma unroll
+    for (int q = 0; q < kGatherRhs; ++q)
+      if (q == lane) { xr = re[q]; xi = im[q]; }
     const double2 s = a.out_scale;
-    double2 o = double2{s.x * re - s.y * im, s.x * im + s.y * re};
-    double2* dst = a.y + (size_t)r * a.n + i;
+    double2 o = double2{s.x * xr - s.y * xi, s.x * xi + s.y * xr};
+    double2* dst = a.y + (size_t)(r0 + lane) * a.n + i;
     if (a.accumulate) {
       const double2 prev = *dst;
       o.x += prev.x;
@@ -449,18 +488,59 @@ static int precision_of(float2*) { return AIM_MIXED; }
 static int precision_of(double2*) { return AIM_FP64_NATIVE; }
 static int precision_of(dfc*) { return AIM_FP64; }
 
+constexpr size_t kMaxDynSmem = 227 * 1024;   // opt-in dynamic shared memory per CTA
+
+// columns per column-pass CTA: the schedule's choice, else the fewest whole tiles of W
+// columns that give at least 128 threads
 template <typename CT, int TPT>
-static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdArgs fa, RowInvArgs ia, int min_row_threads,
-                             cudaStream_t st) {
-  using T2 = CT;
+static int col_cols_of(const Schedule& sc, int logH, int logP) {
   constexpr int W = GridT<CT>::W, LPT = 3 - TPT;
+  if (sc.col_cols > 0) return sc.col_cols;
+  const int tpf = (1 << logH) / 16, ntiles = (1 << logP) / W;
+  int tpc = 1;
+  while (tpc * LPT * W * tpf < 128 && tpc < ntiles) tpc *= 2;
+  return tpc * W;
+}
+
+template <typename CT, int TPT>
+static bool feasible_tpt(const Schedule& sc, int logH, int logP) {
+  constexpr int LPT = 3 - TPT;
+  const int H = 1 << logH, tpf = H / 16, cols = col_cols_of<CT, TPT>(sc, logH, logP);
+  if (cols < 1 || (cols & (cols - 1)) || cols > (1 << logP)) return false;
+  if (LPT * cols * tpf > LaunchMax<CT, TPT>::value || LPT * cols * tpf < 32) return false;
+  if (2 * (size_t)cols * padded_len(H) * sizeof(CT) > kMaxDynSmem) return false;
+  if (sc.min_row_threads < 32 || sc.min_row_threads > 1024) return false;
+  // row passes: one row per CTA must fit too
+  if (2 * (size_t)padded_len(H) * sizeof(CT) > kMaxDynSmem || LPT * tpf > LaunchMax<CT, TPT>::value) return false;
+  return true;
+}
+
+bool schedule_feasible(int precision, int logH, int logP, const Schedule& s) {
+  if (s.tpt != 1 && s.tpt != 2) return false;
+  switch (precision) {
+    case AIM_MIXED: return s.tpt == 1 ? feasible_tpt<float2, 1>(s, logH, logP) : feasible_tpt<float2, 2>(s, logH, logP);
+    case AIM_FP64: return s.tpt == 1 ? feasible_tpt<dfc, 1>(s, logH, logP) : feasible_tpt<dfc, 2>(s, logH, logP);
+    case AIM_FP64_NATIVE: return s.tpt == 2 && feasible_tpt<double2, 2>(s, logH, logP);
+    default: return false;
+  }
+}
+
+template <typename CT, int TPT>
+static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdArgs fa, RowInvArgs ia,
+                             const Schedule& sc, cudaStream_t st) {
+  const int min_row_threads = sc.min_row_threads;
+  using T2 = CT;
+  constexpr int LPT = 3 - TPT;
   const int H = ctx->H, tpf = H / 16, HS = padded_len(H);
   const void* tw = twiddles(ctx, (CT*)nullptr);
   const void* spec = spectrum(ctx, filtered, (CT*)nullptr);
 
-  // rows per CTA: at least min_row_threads threads, within the launch bound
+  // rows per CTA: at least min_row_threads threads (fewer when the grid has fewer rows, but
+  // never less than a full warp: the recombination shuffles need all 32 lanes; rows past the
+  // last one load zeros and store nothing), within the launch bound
   int rpc = 1;
-  while (rpc * LPT * tpf < min_row_threads && rpc < ctx->nrows && 2 * rpc * LPT * tpf <= LaunchMax<CT, TPT>::value)
+  while (((rpc * LPT * tpf < min_row_threads && rpc < ctx->nrows) || rpc * LPT * tpf < 32) &&
+         2 * rpc * LPT * tpf <= LaunchMax<CT, TPT>::value)
     rpc *= 2;
   const int row_blocks = (ctx->nrows + rpc - 1) / rpc;
   const size_t sm_row = 2 * (size_t)rpc * HS * sizeof(T2);
@@ -480,9 +560,9 @@ static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdAr
   AIM_CUDA_TRY(cudaGetLastError());
 
   // column pass
-  const int ntiles = ctx->P / W;
-  int tpc = 1;
-  while (tpc * LPT * W * tpf < 128 && tpc < ntiles) tpc *= 2;
+  const int cols = col_cols_of<CT, TPT>(sc, ctx->logH, ctx->logP);
+  int log_cols = 0;
+  while ((1 << log_cols) < cols) ++log_cols;
   ColArgs ca;
   ca.inter = ctx->inter;
   ca.spec = spec;
@@ -491,12 +571,12 @@ static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdAr
   ca.logP = ctx->logP;
   ca.row_lo = ctx->row_lo;
   ca.nrows = ctx->nrows;
-  ca.tiles_per_cta = tpc;
-  const size_t sm_col = 2 * (size_t)tpc * W * HS * sizeof(T2);
+  ca.log_cols = log_cols;
+  const size_t sm_col = 2 * (size_t)cols * HS * sizeof(T2);
   AIM_TRY(ensure_smem(k_col_conv<CT, TPT>, sm_col));
   {
     ProfScope ps(K_COL_CONV, st);
-    k_col_conv<CT, TPT><<<dim3(ntiles / tpc, channels), tpc * LPT * W * tpf, sm_col, st>>>(ca);
+    k_col_conv<CT, TPT><<<dim3(ctx->P / cols, channels), cols * LPT * tpf, sm_col, st>>>(ca);
   }
   AIM_CUDA_TRY(cudaGetLastError());
 
@@ -524,13 +604,13 @@ static aim_status launch_three_passes(aim_ctx* ctx, int channels, bool filtered,
   if (channels > 65535) return fail(AIM_EINVAL, "too many channels in one grid pass");
   if (ctx->H < 32) return fail(AIM_EINVAL, "embedding side P must be >= 64");
   const int p = precision_of((CT*)nullptr);
-  const int tpt = ctx->sched[p].tpt;
-  const int mrt = ctx->sched[p].min_row_threads;
+  const Schedule sc = ctx->sched[p];
+  if (!schedule_feasible(p, ctx->logH, ctx->logP, sc)) return fail(AIM_EINVAL, "launch schedule not feasible");
   if constexpr (std::is_same<CT, double2>::value) {
-    return launch_tpt<CT, 2>(ctx, channels, filtered, fa, ia, mrt, st);
+    return launch_tpt<CT, 2>(ctx, channels, filtered, fa, ia, sc, st);
   } else {
-    if (tpt == 1) return launch_tpt<CT, 1>(ctx, channels, filtered, fa, ia, mrt, st);
-    return launch_tpt<CT, 2>(ctx, channels, filtered, fa, ia, mrt, st);
+    if (sc.tpt == 1) return launch_tpt<CT, 1>(ctx, channels, filtered, fa, ia, sc, st);
+    return launch_tpt<CT, 2>(ctx, channels, filtered, fa, ia, sc, st);
   }
 }
 
@@ -585,12 +665,17 @@ aim_status grid_pass(aim_ctx* ctx, const PassSpec& spec, int nrhs, const double2
   ga.out_scale = spec.out_scale;
   ga.y = y;
   ga.accumulate = 0;
-  const long long warps = (long long)ctx->n * nrhs;
+  constexpr int kRhsBlock = 8;
+  const int rb = nrhs == 1 ? 1 : kRhsBlock;
+  const long long warps = (long long)ctx->n * ((nrhs + rb - 1) / rb);
   const int tpb = 256;
   const long long blocks = (warps * 32 + tpb - 1) / tpb;
   {
     ProfScope ps(K_GATHER, st);
-    k_gather<VT><<<(unsigned)blocks, tpb, 0, st>>>(ga);
+    if (rb == 1)
+      k_gather<VT, 1><<<(unsigned)blocks, tpb, 0, st>>>(ga);
+    else
+      k_gather<VT, kRhsBlock><<<(unsigned)blocks, tpb, 0, st>>>(ga);
   }
   AIM_CUDA_TRY(cudaGetLastError());
   return AIM_OK;

@@ -76,8 +76,17 @@ class SolveResult:
 class Server:
     """Admission by device-memory budget, `slots` concurrent solves, resident context cache."""
 
-    def __init__(self, memory_budget_bytes: int, slots: int = 4, max_cached: int = 16, device: int = 0):
+    def __init__(self, memory_budget_bytes: int, slots: int = 4, max_cached: int = 16, device: int = 0,
+                 policy: str = "sjf", max_wait_s: float = 30.0):
+        """policy "fifo": the first queued request that fits. policy "sjf": the fitting request
+        with the least estimated work (right-hand sides x grid cells x unknowns, which tracks
+        the grid work per iteration times the iteration count), except that requests waiting
+        longer than max_wait_s go first, oldest first, so that large requests are not starved."""
         import torch
+        if policy not in ("fifo", "sjf"):
+            raise ValueError("policy must be 'fifo' or 'sjf'")
+        self.policy = policy
+        self.max_wait_s = float(max_wait_s)
         self.torch = torch
         self.budget = int(memory_budget_bytes)
         self.slots = int(slots)
@@ -150,9 +159,26 @@ class Server:
             self._cache_bytes -= b
             ctx.close()
 
+    @staticmethod
+    def _work(req: SolveRequest) -> float:
+        P = req.fft_P if req.fft_P > 0 else 2 * req.m
+        return float(len(req.angles)) * P * P * len(req.nodes)
+
+    def _order(self):
+        """Queue indices in the order the policy considers them."""
+        idx = list(range(len(self._queue)))
+        if self.policy == "fifo":
+            return idx
+        now = time.perf_counter()
+        old = [i for i in idx if now - self._queue[i][0].arrival > self.max_wait_s]
+        young = sorted((i for i in idx if now - self._queue[i][0].arrival <= self.max_wait_s),
+                       key=lambda i: (self._work(self._queue[i][0]), self._queue[i][0].arrival))
+        return old + young
+
     def _admit(self):
-        """Called with the lock held: the first queued request that fits (FIFO among fitting)."""
-        for idx, (req, need) in enumerate(self._queue):
+        """Called with the lock held: the first request in policy order that fits the budget."""
+        for idx in self._order():
+            req, need = self._queue[idx]
             key = req.key()
             cached = key in self._cache
             extra = 0 if cached else need
@@ -202,6 +228,9 @@ class Server:
                 x_host = x.cpu().numpy()
             except aim.AimError as e:
                 status = e.status
+                ctx = None
+            except Exception:   # anything else (e.g. an allocation failure) fails this request only
+                status = aim.ECUDA
                 ctx = None
             done = time.perf_counter()
             with self._lock:

@@ -68,6 +68,14 @@ def test_setup_rejects_bad_arguments_before_touching_the_gpu(lib):
         aim.Context(nodes[:2], 2 * np.pi, aim.TE, 32)
 
 
+def test_schedule_calls_reject_null_arguments(lib):
+    from paper_2606_10784_gb300 import aim
+    sc = aim.Schedule(1, 128, 0)
+    assert lib.aim_set_schedule(None, 0, ctypes.byref(sc)) == aim.EINVAL
+    assert lib.aim_get_schedule(None, 0, ctypes.byref(sc)) == aim.EINVAL
+    assert lib.aim_autotune(None, 1, 0, None, None) == aim.EINVAL
+
+
 def test_binding_refuses_to_run_without_the_library(monkeypatch, tmp_path):
     from paper_2606_10784_gb300 import aim
     monkeypatch.setattr(aim, "_lib", None)

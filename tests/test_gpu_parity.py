@@ -265,5 +265,47 @@ def test_autotuned_schedule_gives_identical_results(te_pair, precision):
     before = run_matvec(ctx, "calderon_alpha", x, precision=precision)
     chosen = ctx.autotune(nrhs=2, precision=precision)
     assert chosen["transforms_per_thread"] in (1, 2)
+    assert chosen == ctx.get_schedule(precision)
     after = run_matvec(ctx, "calderon_alpha", x, precision=precision)
     assert np.array_equal(before, after)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("op", ["S_alpha", "N", "calderon_alpha"])
+def test_batched_matvec_equals_single_rhs_calls(te_pair, precision, op):
+    # 11 right-hand sides: one gather block of 8 and a ragged block of 3; every channel of a
+    # batched launch does the arithmetic of a single-vector call, bit for bit
+    nodes, ctx, ref = te_pair
+    x = synth.random_coeffs(len(nodes), 11, seed=23)
+    batched = run_matvec(ctx, op, x, precision=precision)
+    for r in range(11):
+        assert np.array_equal(batched[r], run_matvec(ctx, op, x[r:r + 1], precision=precision)[0]), r
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_every_feasible_schedule_gives_identical_results(te_pair, aimlib, precision):
+    # one or two transforms per thread, row-pass CTAs of 32..1024 threads, 1..32 columns per
+    # column-pass CTA (fewer than a 32-byte tile, a tile, several tiles): same bits every time
+    nodes, ctx, ref = te_pair
+    x = synth.random_coeffs(len(nodes), 3, seed=22)
+    saved = ctx.get_schedule(precision)
+    want = None
+    ran = refused = 0
+    for tpt in (1, 2):
+        for rows in (32, 128, 1024):
+            for cols in (0, 1, 2, 4, 8, 32):
+                try:
+                    ctx.set_schedule(precision, tpt, rows, cols)
+                except aimlib.AimError as e:
+                    assert e.status == aimlib.EINVAL
+                    refused += 1
+                    continue
+                got = run_matvec(ctx, "calderon_alpha", x, precision=precision)
+                if want is None:
+                    want = got
+                assert np.array_equal(got, want), (tpt, rows, cols)
+                ran += 1
+    ctx.set_schedule(precision, **saved)
+    assert ran >= 6 and refused >= 1
+    tol = TOL32 if precision == 1 else TOL64
+    assert rel(want[0], ref.calderon(x[0], True)) < tol

@@ -327,3 +327,30 @@ def test_aim_calderon_solution_matches_series():
     ref = special.te_cylinder_current(2 * math.pi * np.arange(N) / N, K, 1.0)
     assert rel(x, ref) < 5e-3
     assert it < 40
+
+
+# --------------------------------------------------------------------------------------
+# printed table values (tests/golden): the Green's function and the n = 0 circle eigenvalues
+# --------------------------------------------------------------------------------------
+def _bessel_table():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "bessel_table_9_1.txt")
+    return np.loadtxt(path, comments="#")
+
+
+def test_green_function_against_printed_bessel_table():
+    # g = -(j/4) H0^(2)(kr) with H0^(2) = J0 - j Y0 (Sec. II): Re g = -Y0/4, Im g = -J0/4
+    for x, j0, j1, y0, y1 in _bessel_table():
+        g = special.green(1.0, np.array([x]))[0]
+        assert abs(g - (-0.25 * y0 - 0.25j * j0)) < 1e-10
+
+
+def test_circle_eigenvalues_n0_against_printed_bessel_table():
+    # lambda_0 = -(j pi a/2) J0(ka) H0^(2)(ka); mu_0 = (j pi a k^2/2) J0'(ka) H0^(2)'(ka) with
+    # J0' = -J1, Y0' = -Y1 (Graf's addition theorem for the circle of radius a)
+    a = 1.0
+    for x, j0, j1, y0, y1 in _bessel_table():
+        lam = -0.5j * math.pi * a * j0 * (j0 - 1j * y0)
+        mu = 0.5j * math.pi * a * x * x * (-j1) * (-j1 + 1j * y1)
+        assert abs(special.circle_lambda(0, x, a) - lam) < 1e-9 * max(1.0, abs(lam))
+        assert abs(special.circle_mu(0, x, a) - mu) < 1e-9 * max(1.0, abs(mu))
