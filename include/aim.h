@@ -125,9 +125,9 @@ typedef struct {
   int max_iter;        /* total inner iterations per right-hand side */
   int precision;       /* AIM_FP64, AIM_FP64_NATIVE, or AIM_MIXED (FP32 grid inner solves inside
                           iterative refinement with AIM_FP64 residuals) */
-  double inner_tol;    /* mixed only: relative tolerance of each inner FP32-grid solve; <= 0 asks for
-                          just the remaining reduction, 0.9 tol ||b|| / ||r||, but at least 1e-5
-                          (the complex64 product's noise floor on nearly singular systems) */
+  double inner_tol;    /* mixed only: tolerance of each inner FP32-grid solve, on its Arnoldi residual
+                          estimate relative to ||r|| (one Krylov cycle of at most `restart`
+                          iterations); <= 0 asks for half the remaining reduction, 0.5 tol ||b||/||r|| */
   int timeout_ms;      /* <= 0: no limit */
 } aim_solve_opts;
 
@@ -178,12 +178,15 @@ aim_status aim_reserve(aim_ctx* ctx, int nrhs, int precision);
  * adjacent lanes, 2 puts both in one thread (native FP64 allows 2 only). row_threads: the
  * least threads of a row-pass CTA (32..1024; rows are added to a CTA until it has that many).
  * col_cols: columns of one column-pass CTA, a power of two, 0 for the default (the fewest
- * whole 32-byte column tiles that give 128 threads). Results are identical under every
- * schedule: the arithmetic and its order do not depend on it. */
+ * whole 32-byte column tiles that give 128 threads). elems_per_thread: 16 (radix-16 passes)
+ * or 8 (radix-8 passes, half the registers per thread; not for native FP64); 0 means 16.
+ * Results are identical under every schedule with the same elems_per_thread: the arithmetic
+ * and its order do not depend on the rest; the two pass geometries differ by rounding. */
 typedef struct {
   int transforms_per_thread;
   int row_threads;
   int col_cols;
+  int elems_per_thread;
 } aim_schedule;
 
 /* Sets the schedule of `precision` for this context. AIM_EINVAL when it cannot be launched
@@ -192,8 +195,9 @@ aim_status aim_set_schedule(aim_ctx* ctx, int precision, const aim_schedule* sch
 aim_status aim_get_schedule(const aim_ctx* ctx, int precision, aim_schedule* schedule);
 
 /* Autotuner (no counterpart in the paper; a launch-schedule choice). Times the filtered
- * product (S^alpha) for nrhs vectors under each feasible schedule - one or two transforms
- * per thread, 128 or 256 row-pass threads, and 1 to 8 columns per column-pass CTA - and
+ * product (S^alpha) for nrhs vectors under each feasible schedule - 16 or 8 elements and one
+ * or two transforms per thread, 128 or 256 row-pass threads, 1 to 8 columns per column-pass
+ * CTA - and
  * keeps the fastest for this context and precision. Synchronises `stream`. *chosen (host,
  * may be NULL) receives the winner. */
 aim_status aim_autotune(aim_ctx* ctx, int nrhs, int precision, void* stream, aim_schedule* chosen);

@@ -62,11 +62,12 @@ class Info(ctypes.Structure):
 
 
 class Schedule(ctypes.Structure):
-    _fields_ = [("transforms_per_thread", ctypes.c_int), ("row_threads", ctypes.c_int), ("col_cols", ctypes.c_int)]
+    _fields_ = [("transforms_per_thread", ctypes.c_int), ("row_threads", ctypes.c_int), ("col_cols", ctypes.c_int),
+                ("elems_per_thread", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         return {"transforms_per_thread": self.transforms_per_thread, "row_threads": self.row_threads,
-                "col_cols": self.col_cols}
+                "col_cols": self.col_cols, "elems_per_thread": self.elems_per_thread}
 
 
 class KernelStat(ctypes.Structure):
@@ -243,8 +244,9 @@ class Context:
                "aim_autotune")
         return chosen.as_dict()
 
-    def set_schedule(self, precision: int, transforms_per_thread: int, row_threads: int, col_cols: int = 0):
-        sc = Schedule(int(transforms_per_thread), int(row_threads), int(col_cols))
+    def set_schedule(self, precision: int, transforms_per_thread: int, row_threads: int, col_cols: int = 0,
+                     elems_per_thread: int = 16):
+        sc = Schedule(int(transforms_per_thread), int(row_threads), int(col_cols), int(elems_per_thread))
         _check(lib().aim_set_schedule(self._h, int(precision), ctypes.byref(sc)), "aim_set_schedule")
 
     def get_schedule(self, precision: int) -> dict:

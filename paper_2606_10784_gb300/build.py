@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libaimgb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["capi.cu", "setup_host.cpp", "setup_kernels.cu", "matvec_kernels.cu", "solver.cu", "prof.cu", "noalloc.cu"]
+SOURCES = ["capi.cu", "setup_host.cpp", "setup_kernels.cu", "matvec_common.cu", "matvec_dfc.cu", "matvec_f32.cu",
+           "matvec_f64.cu", "solver.cu", "prof.cu", "noalloc.cu"]
 
 
 def nvcc() -> str:

@@ -44,7 +44,8 @@ enum KernelId {
 };
 void count_launches(int id, int n);   // counted, not timed
 struct ProfScope {
-  ProfScope(int id, cudaStream_t st);
+  // count_launch = false: a timing-only scope around a group of launches counted elsewhere
+  ProfScope(int id, cudaStream_t st, bool count_launch = true);
   ~ProfScope();
   int id;
   cudaStream_t st;
@@ -95,12 +96,14 @@ struct NearField {
 };
 
 // Launch schedule of the grid kernels for one precision: transforms per thread (1: even/odd
-// halves in adjacent lanes, 2: both in one thread), the minimum threads of a row-pass CTA, and
-// the columns of a column-pass CTA (0: the fewest whole tiles that give 128 threads).
+// halves in adjacent lanes, 2: both in one thread), the minimum threads of a row-pass CTA, the
+// columns of a column-pass CTA (0: the fewest whole tiles that give 128 threads), and the
+// elements each thread owns per transform (16 or 8; 0 means 16).
 struct Schedule {
   int tpt;
   int min_row_threads;
   int col_cols;
+  int elems;
 };
 
 // Whether a schedule can be launched for a context whose transforms have length H = 2^logH
@@ -159,7 +162,8 @@ struct aim_ctx {
   double* red_host = nullptr; size_t red_host_bytes = 0;
   int reserved_rhs[3] = {0, 0, 0};   // per precision (AIM_FP64, AIM_MIXED, AIM_FP64_NATIVE)
   // launch schedule per precision; defaults measured on GB300, aim_autotune re-measures
-  aim::Schedule sched[3] = {{1, 128, 0}, {2, 128, 0}, {2, 128, 0}};
+  // defaults: measured at the single-solve scale (2048^2 grid, P = 4096), feasible at every P
+  aim::Schedule sched[3] = {{1, 128, 0, 8}, {2, 128, 0, 16}, {2, 128, 0, 16}};
   // bookkeeping
   std::vector<void*> allocations;
   size_t device_bytes = 0;

@@ -350,7 +350,8 @@ aim_status aim_reserve(aim_ctx* ctx, int nrhs, int precision) {
 aim_status aim_set_schedule(aim_ctx* ctx, int precision, const aim_schedule* schedule) {
   if (!ctx || !schedule) return fail(AIM_EINVAL, "bad argument");
   if (precision < AIM_FP64 || precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "precision must be 0, 1 or 2");
-  const Schedule sc{schedule->transforms_per_thread, schedule->row_threads, schedule->col_cols};
+  const Schedule sc{schedule->transforms_per_thread, schedule->row_threads, schedule->col_cols,
+                    schedule->elems_per_thread};
   if (!schedule_feasible(precision, ctx->logH, ctx->logP, sc))
     return fail(AIM_EINVAL, "schedule cannot be launched for this transform length");
   ctx->sched[precision] = sc;
@@ -361,7 +362,7 @@ aim_status aim_get_schedule(const aim_ctx* ctx, int precision, aim_schedule* sch
   if (!ctx || !schedule) return fail(AIM_EINVAL, "bad argument");
   if (precision < AIM_FP64 || precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "precision must be 0, 1 or 2");
   const Schedule& sc = ctx->sched[precision];
-  *schedule = aim_schedule{sc.tpt, sc.min_row_threads, sc.col_cols};
+  *schedule = aim_schedule{sc.tpt, sc.min_row_threads, sc.col_cols, sc.elems == 0 ? 16 : sc.elems};
   return AIM_OK;
 }
 
@@ -382,11 +383,13 @@ aim_status aim_autotune(aim_ctx* ctx, int nrhs, int precision, void* stream, aim
   const int tpts[2] = {1, 2};
   const int rows[2] = {128, 256};
   const int cols[5] = {0, 1, 2, 4, 8};
+  const int elems[2] = {16, 8};
   aim_status s = AIM_OK;
+  for (int e = 0; e < 2 && s == AIM_OK; ++e)
   for (int a = 0; a < 2 && s == AIM_OK; ++a)
     for (int b = 0; b < 2 && s == AIM_OK; ++b)
       for (int cc = 0; cc < 5 && s == AIM_OK; ++cc) {
-        const Schedule cand{tpts[a], rows[b], cols[cc]};
+        const Schedule cand{tpts[a], rows[b], cols[cc], elems[e]};
         if (!schedule_feasible(precision, ctx->logH, ctx->logP, cand)) continue;
         ctx->sched[precision] = cand;
         s = apply_op(ctx, AIM_OP_S_ALPHA, nrhs, ctx->stage_in, ctx->stage_out, precision, st);   // warm
@@ -408,7 +411,7 @@ aim_status aim_autotune(aim_ctx* ctx, int nrhs, int precision, void* stream, aim
   ctx->sched[precision] = s == AIM_OK ? best : saved;
   if (chosen) {
     const Schedule& w = ctx->sched[precision];
-    *chosen = aim_schedule{w.tpt, w.min_row_threads, w.col_cols};
+    *chosen = aim_schedule{w.tpt, w.min_row_threads, w.col_cols, w.elems == 0 ? 16 : w.elems};
   }
   return s;
 }

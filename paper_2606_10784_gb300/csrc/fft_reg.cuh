@@ -1,13 +1,13 @@
 // Register-resident FFT passes for the AIM grid product (Eq. 8 / Eq. 10).
 //
-// A length-H = 2^logH transform (H >= 16) is split into radix-16 passes plus at most one
-// radix-2/4/8 pass (logH = 4q + rem). Each thread owns 16 elements of every transform it works
-// on: one radix-16 butterfly, or 16/R butterflies of a smaller radix. Butterflies follow the
-// Stockham auto-sort indexing (natural order in and out): butterfly b of a pass with current
-// sub-length Ns reads X[b + r H/R], multiplies by W_{Ns R}^{(b mod Ns) r}, does a length-R DFT
-// in registers and writes X[(b - b mod Ns) R + b mod Ns + r Ns].
-// Shared memory holds the exchange between passes, padded by one element every 16 so that
-// the stride-R writes of the first passes do not collide in banks. Twiddles come from the
+// Each thread owns E = 2^LOGE elements (E = 16 or 8) of every transform it works on. A
+// length-H = 2^logH transform is split into radix-E passes plus at most one pass of a smaller
+// radix (logH = q LOGE + rem); in a radix-R pass a thread does E/R butterflies. Butterflies
+// follow the Stockham auto-sort indexing (natural order in and out): butterfly b of a pass with
+// current sub-length Ns reads X[b + r H/R], multiplies by W_{Ns R}^{(b mod Ns) r}, does a
+// length-R DFT in registers and writes X[(b - b mod Ns) R + b mod Ns + r Ns].
+// Shared memory holds the exchange between passes, padded by one element every E so that the
+// stride-E writes of the first pass do not collide in banks. Twiddles come from the
 // host-computed FP64 table tw[t] = exp(-2 pi i t/P).
 #pragma once
 
@@ -17,11 +17,12 @@
 
 namespace aim {
 
-constexpr int kPadShift = 4;
-__host__ __device__ __forceinline__ int padi(int i) { return i + (i >> kPadShift); }
+template <int LOGE>
+__host__ __device__ __forceinline__ int padi(int i) { return i + (i >> LOGE); }
 // Stride between the transforms of a CTA: the padded length plus 2, so that transforms whose
-// lanes share a warp (the W columns of a tile) start 4 (8-byte) or 2 (16-byte) banks apart.
-__host__ __device__ __forceinline__ int padded_len(int H) { return H + (H >> kPadShift) + 2; }
+// lanes share a warp (the even/odd halves and the columns of a tile) start 2 elements apart.
+template <int LOGE>
+__host__ __device__ __forceinline__ int padded_len(int H) { return H + (H >> LOGE) + 2; }
 
 // read-only load of a twiddle / spectrum entry
 __device__ __forceinline__ float2 ldro(const float2* p) { return __ldg(p); }
@@ -137,17 +138,19 @@ __device__ __forceinline__ void bfly(T2 (&v)[1 << LOGR], int k, int logNs, const
   dft_reg<R, INV>(v);
 }
 
-__device__ __forceinline__ int fft_npass(int logH) { return (logH >> 2) + ((logH & 3) != 0); }
-__device__ __forceinline__ int fft_logr(int pass, int logH) { return pass < (logH >> 2) ? 4 : (logH & 3); }
+template <int LOGE>
+__device__ __forceinline__ int fft_npass(int logH) { return logH / LOGE + (logH % LOGE != 0); }
+template <int LOGE>
+__device__ __forceinline__ int fft_logr(int pass, int logH) { return pass < logH / LOGE ? LOGE : logH % LOGE; }
 
 // One pass over NF transforms owned by this thread group, shared memory in and out.
-// Each thread works on butterflies b = j + t*tpf (t < 16/R) of each of its transforms, whose
+// Each thread works on butterflies b = j + t*tpf (t < E/R) of each of its transforms, whose
 // padded bases in shared memory are fb[f]. `post(f, out_index, value)` may rewrite a value
 // before it is stored (identity for plain passes). Barrier before and after the stores.
-template <int LOGR, bool INV, int NF, typename T2, typename Post>
+template <int LOGR, bool INV, int NF, int LOGE, typename T2, typename Post>
 __device__ __forceinline__ void smem_pass(T2* __restrict__ sm, const int (&fb)[NF], int j, int tpf, int logH,
                                           int logNs, const T2* __restrict__ tw, int logP, Post post) {
-  constexpr int R = 1 << LOGR, NB = 16 >> LOGR;
+  constexpr int R = 1 << LOGR, NB = (1 << LOGE) >> LOGR;
   const int lognb = logH - LOGR;
   const int nsm = (1 << logNs) - 1;
   T2 v[NF][NB][R];
@@ -157,7 +160,7 @@ __device__ __forceinline__ void smem_pass(T2* __restrict__ sm, const int (&fb)[N
     for (int t = 0; t < NB; ++t) {
       const int b = j + t * tpf;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[f][t][r] = sm[fb[f] + padi(b + (r << lognb))];
+      for (int r = 0; r < R; ++r) v[f][t][r] = sm[fb[f] + padi<LOGE>(b + (r << lognb))];
       bfly<LOGR, INV>(v[f][t], b & nsm, logNs, tw, logP);
     }
   __syncthreads();
@@ -171,7 +174,7 @@ __device__ __forceinline__ void smem_pass(T2* __restrict__ sm, const int (&fb)[N
 #pragma unroll
       for (int r = 0; r < R; ++r) {
         const int o = base + (r << logNs);
-        sm[fb[f] + padi(o)] = post(f, o, v[f][t][r]);
+        sm[fb[f] + padi<LOGE>(o)] = post(f, o, v[f][t][r]);
       }
     }
   __syncthreads();
@@ -179,10 +182,10 @@ __device__ __forceinline__ void smem_pass(T2* __restrict__ sm, const int (&fb)[N
 
 // Last pass: shared memory in, `emit(t, r, out_index, values[NF])` out (no stores to shared
 // memory here; callers that write shared memory in `emit` must place a barrier first).
-template <int LOGR, bool INV, int NF, typename T2, typename Emit>
+template <int LOGR, bool INV, int NF, int LOGE, typename T2, typename Emit>
 __device__ __forceinline__ void last_pass(const T2* __restrict__ sm, const int (&fb)[NF], int j, int tpf, int logH,
                                           int logNs, const T2* __restrict__ tw, int logP, Emit emit) {
-  constexpr int R = 1 << LOGR, NB = 16 >> LOGR;
+  constexpr int R = 1 << LOGR, NB = (1 << LOGE) >> LOGR;
   const int lognb = logH - LOGR;
   const int nsm = (1 << logNs) - 1;
 #pragma unroll
@@ -193,7 +196,7 @@ __device__ __forceinline__ void last_pass(const T2* __restrict__ sm, const int (
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[f][r] = sm[fb[f] + padi(b + (r << lognb))];
+      for (int r = 0; r < R; ++r) v[f][r] = sm[fb[f] + padi<LOGE>(b + (r << lognb))];
       bfly<LOGR, INV>(v[f], k, logNs, tw, logP);
     }
     const int base = ((b - k) << LOGR) + k;
@@ -208,29 +211,36 @@ __device__ __forceinline__ void last_pass(const T2* __restrict__ sm, const int (
 }
 
 // Runs passes [p0, p1) of a length-2^logH transform in shared memory, dispatching the radix.
-template <bool INV, int NF, typename T2, typename Post>
+template <bool INV, int NF, int LOGE, typename T2, typename Post>
 __device__ __forceinline__ void smem_passes(T2* sm, const int (&fb)[NF], int j, int tpf, int logH, int p0, int p1,
                                             int logNs, const T2* tw, int logP, Post post) {
   for (int p = p0; p < p1; ++p) {
-    const int lr = fft_logr(p, logH);
-    switch (lr) {
-      case 4: smem_pass<4, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, post); break;
-      case 3: smem_pass<3, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, post); break;
-      case 2: smem_pass<2, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, post); break;
-      default: smem_pass<1, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, post); break;
+    const int lr = fft_logr<LOGE>(p, logH);
+    if (lr == LOGE) {
+      smem_pass<LOGE, INV, NF, LOGE>(sm, fb, j, tpf, logH, logNs, tw, logP, post);
+    } else {
+      switch (lr) {
+        case 3: if constexpr (LOGE > 3) smem_pass<3, INV, NF, LOGE>(sm, fb, j, tpf, logH, logNs, tw, logP, post); break;
+        case 2: smem_pass<2, INV, NF, LOGE>(sm, fb, j, tpf, logH, logNs, tw, logP, post); break;
+        default: smem_pass<1, INV, NF, LOGE>(sm, fb, j, tpf, logH, logNs, tw, logP, post); break;
+      }
     }
     logNs += lr;
   }
 }
 
-template <bool INV, int NF, typename T2, typename Emit>
+template <bool INV, int NF, int LOGE, typename T2, typename Emit>
 __device__ __forceinline__ void last_pass_dispatch(const T2* sm, const int (&fb)[NF], int j, int tpf, int logH,
                                                    int logNs, const T2* tw, int logP, Emit emit) {
-  switch (fft_logr(fft_npass(logH) - 1, logH)) {
-    case 4: last_pass<4, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, emit); break;
-    case 3: last_pass<3, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, emit); break;
-    case 2: last_pass<2, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, emit); break;
-    default: last_pass<1, INV, NF>(sm, fb, j, tpf, logH, logNs, tw, logP, emit); break;
+  const int lr = fft_logr<LOGE>(fft_npass<LOGE>(logH) - 1, logH);
+  if (lr == LOGE) {
+    last_pass<LOGE, INV, NF, LOGE>(sm, fb, j, tpf, logH, logNs, tw, logP, emit);
+  } else {
+    switch (lr) {
+      case 3: if constexpr (LOGE > 3) last_pass<3, INV, NF, LOGE>(sm, fb, j, tpf, logH, logNs, tw, logP, emit); break;
+      case 2: last_pass<2, INV, NF, LOGE>(sm, fb, j, tpf, logH, logNs, tw, logP, emit); break;
+      default: last_pass<1, INV, NF, LOGE>(sm, fb, j, tpf, logH, logNs, tw, logP, emit); break;
+    }
   }
 }
 
@@ -238,13 +248,13 @@ __device__ __forceinline__ void last_pass_dispatch(const T2* sm, const int (&fb)
 // pass of the inverse transform, in registers. The last Stockham pass (Ns = H/R) of butterfly b
 // writes the outputs X[b + r H/R], which are exactly the inputs of butterfly b of an inverse
 // pass with the same radix R and Ns = 1. So when the inverse runs its radices in the reverse
-// order (R first, then the radix-16 passes), nothing goes through shared memory between the
+// order (R first, then the radix-E passes), nothing goes through shared memory between the
 // two. `mul(f, k, value)` multiplies forward output k of transform f. The inverse pass writes
 // its outputs (index b R + r) to shared memory: barrier before and after the stores.
-template <int LOGR, int NF, typename T2, typename Mul>
+template <int LOGR, int NF, int LOGE, typename T2, typename Mul>
 __device__ __forceinline__ void conv_mid_pass(T2* __restrict__ sm, const int (&fb)[NF], int j, int tpf, int logH,
                                               const T2* __restrict__ tw, int logP, Mul mul) {
-  constexpr int R = 1 << LOGR, NB = 16 >> LOGR;
+  constexpr int R = 1 << LOGR, NB = (1 << LOGE) >> LOGR;
   const int lognb = logH - LOGR;
   T2 v[NF][NB][R];
 #pragma unroll
@@ -253,7 +263,7 @@ __device__ __forceinline__ void conv_mid_pass(T2* __restrict__ sm, const int (&f
     for (int t = 0; t < NB; ++t) {
       const int b = j + t * tpf;
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[f][t][r] = sm[fb[f] + padi(b + (r << lognb))];
+      for (int r = 0; r < R; ++r) v[f][t][r] = sm[fb[f] + padi<LOGE>(b + (r << lognb))];
       bfly<LOGR, false>(v[f][t], b, lognb, tw, logP);   // Ns = H/R, so b mod Ns = b
 #pragma unroll
       for (int r = 0; r < R; ++r) v[f][t][r] = mul(f, b + (r << lognb), v[f][t][r]);
@@ -266,9 +276,24 @@ __device__ __forceinline__ void conv_mid_pass(T2* __restrict__ sm, const int (&f
     for (int t = 0; t < NB; ++t) {
       const int b = j + t * tpf;
 #pragma unroll
-      for (int r = 0; r < R; ++r) sm[fb[f] + padi((b << LOGR) + r)] = v[f][t][r];
+      for (int r = 0; r < R; ++r) sm[fb[f] + padi<LOGE>((b << LOGR) + r)] = v[f][t][r];
     }
   __syncthreads();
+}
+
+// conv_mid_pass for the radix lr of the last forward pass
+template <int NF, int LOGE, typename T2, typename Mul>
+__device__ __forceinline__ void conv_mid_dispatch(int lr, T2* sm, const int (&fb)[NF], int j, int tpf, int logH,
+                                                  const T2* tw, int logP, Mul mul) {
+  if (lr == LOGE) {
+    conv_mid_pass<LOGE, NF, LOGE>(sm, fb, j, tpf, logH, tw, logP, mul);
+  } else {
+    switch (lr) {
+      case 3: if constexpr (LOGE > 3) conv_mid_pass<3, NF, LOGE>(sm, fb, j, tpf, logH, tw, logP, mul); break;
+      case 2: conv_mid_pass<2, NF, LOGE>(sm, fb, j, tpf, logH, tw, logP, mul); break;
+      default: conv_mid_pass<1, NF, LOGE>(sm, fb, j, tpf, logH, tw, logP, mul); break;
+    }
+  }
 }
 
 struct Identity {

@@ -12,8 +12,9 @@ namespace aim {
 template <typename CT> struct GridT;
 // W: column-tile width (W * sizeof(CT) = 32 bytes); VT: type of restricted grid values handed
 // to the gather; MaxThreads: launch bound (16-byte types hold 32 x 16 bytes per thread).
-// MaxThreads is the launch bound with one transform per thread (TPT = 1); with two transforms
-// per thread (TPT = 2) a CTA of the same work has half the threads.
+// MaxThreads is the launch bound with one transform of 16 elements per thread (TPT = 1); with two
+// transforms per thread (TPT = 2) a CTA of the same work has half the threads, with 8 elements
+// per thread twice as many (at most 1024).
 template <> struct GridT<float2> {
   using VT = float2;
   static constexpr int W = 4, MaxThreads = 1024;
@@ -29,8 +30,11 @@ template <> struct GridT<dfc> {
 // a double-float complex product is ~40 FP32-pipe instructions: twiddles come whole from the table
 template <> struct TwiddleFromTable<dfc> { static constexpr bool value = true; };
 
-template <typename CT, int TPT> struct LaunchMax {
-  static constexpr int value = TPT == 1 ? GridT<CT>::MaxThreads : GridT<CT>::MaxThreads / 2;
+template <typename CT, int TPT, int LOGE> struct LaunchMax {
+  // fewer elements per thread: the same registers per thread hold the work of fewer elements,
+  // so the same register file holds more threads
+  static constexpr int base = TPT == 1 ? GridT<CT>::MaxThreads : GridT<CT>::MaxThreads / 2;
+  static constexpr int value = (base << (4 - LOGE)) > 1024 ? 1024 : (base << (4 - LOGE));
 };
 
 template <typename CT> __device__ __forceinline__ CT czero();

@@ -1,0 +1,10 @@
+// The grid product (Eq. 8 / Eq. 10) compiled for double-float complex (FP64 mode) grid arithmetic. One translation unit per
+// element type keeps the build parallel.
+#include "matvec_kernels.cuh"
+
+namespace aim {
+
+template aim_status grid_pass<dfc>(aim_ctx*, const PassSpec&, int, const double2*, double2*, cudaStream_t);
+template aim_status grid_product_dense<dfc>(aim_ctx*, bool, int, const double2*, double2*, cudaStream_t);
+
+}  // namespace aim

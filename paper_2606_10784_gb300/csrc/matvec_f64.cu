@@ -1,0 +1,10 @@
+// The grid product (Eq. 8 / Eq. 10) compiled for IEEE binary64 complex (native FP64 mode) grid arithmetic. One translation unit per
+// element type keeps the build parallel.
+#include "matvec_kernels.cuh"
+
+namespace aim {
+
+template aim_status grid_pass<double2>(aim_ctx*, const PassSpec&, int, const double2*, double2*, cudaStream_t);
+template aim_status grid_product_dense<double2>(aim_ctx*, bool, int, const double2*, double2*, cudaStream_t);
+
+}  // namespace aim

@@ -15,7 +15,8 @@
 //               grid points the test projection reads (the restriction [.]_restr).
 //   k_gather    y_i = sum over projections of coef * (P_t^T v)_i plus the near-field row
 //               (C x)_i, one warp per unknown, deterministic.
-// Each length-H transform runs as register-resident radix-16 passes (fft_reg.cuh): the first
+// Each length-H transform runs as register-resident radix-E passes (fft_reg.cuh, E = 16 or 8
+// elements per thread, a schedule choice): the first
 // pass reads its operands straight from global memory (column and inverse row passes) and the
 // last pass writes straight to global memory, so shared memory carries only the exchanges
 // between passes. A thread owns TPT transforms: with TPT = 2 the even- and odd-half transforms
@@ -25,7 +26,9 @@
 // The intermediate m x P grid of a channel is stored as column tiles of W entries
 // (W * sizeof(complex) = 32 bytes) so that the column pass reads contiguous blocks and the
 // row passes touch whole 32-byte sectors. Only grid rows that hold active points are stored.
-#include <chrono>
+#pragma once
+
+#include <type_traits>
 
 #include "aim_internal.h"
 #include "gridtypes.cuh"
@@ -50,14 +53,14 @@ struct RowFwdArgs {
   int rows_per_cta;
 };
 
-// CTA: rows_per_cta rows of one channel; (3 - TPT) * H/16 threads per row.
-template <typename CT, int TPT>
-__global__ void __launch_bounds__(LaunchMax<CT, TPT>::value) k_row_fwd(RowFwdArgs a) {
+// CTA: rows_per_cta rows of one channel; (3 - TPT) * H/E threads per row (E = 2^LOGE elements each).
+template <typename CT, int TPT, int LOGE>
+__global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_fwd(RowFwdArgs a) {
   using T2 = CT;
   constexpr int W = GridT<CT>::W, NF = TPT, LPT = 3 - TPT;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
-  const int H = 1 << a.logH, P = 1 << a.logP, tpf = H >> 4, HS = padded_len(H);
+  const int H = 1 << a.logH, P = 1 << a.logP, tpf = H >> LOGE, HS = padded_len<LOGE>(H);
   const int per_row = LPT * tpf;
   const int g = threadIdx.x / per_row, rem = threadIdx.x - g * per_row;
   const int half = TPT == 1 ? (rem & 1) : 0, j = TPT == 1 ? (rem >> 1) : rem;
@@ -78,7 +81,7 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT>::value) k_row_fwd(RowFwdArg
       const double2* u = a.x + (size_t)c * a.m * a.m + (size_t)iy * a.m;
       for (int ix = rem; ix < a.m; ix += per_row) {
         const double2 v = u[ix];
-        sm[fbA + padi(ix)] = cfrom<T2>(v.x, v.y);
+        sm[fbA + padi<LOGE>(ix)] = cfrom<T2>(v.x, v.y);
       }
     } else {
       const int pj = c / a.nrhs, r = c - pj * a.nrhs;
@@ -94,38 +97,38 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT>::value) k_row_fwd(RowFwdArg
           re = fma(ww, xx.x, re);
           im = fma(ww, xx.y, im);
         }
-        sm[fbA + padi(a.act_ix[ap])] = cfrom<T2>(re, im);
+        sm[fbA + padi<LOGE>(a.act_ix[ap])] = cfrom<T2>(re, im);
       }
     }
   }
   __syncthreads();
-  // pass 0 (radix 16, Ns = 1): the transform of a and/or of a w^n
+  // pass 0 (radix E, Ns = 1): the transform of a and/or of a w^n
   {
-    const int lognb = a.logH - 4;
-    T2 v[NF][16];
+    const int lognb = a.logH - LOGE;
+    T2 v[NF][1 << LOGE];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
+    for (int r = 0; r < (1 << LOGE); ++r) {
       const int nn = j + (r << lognb);
-      const T2 x = sm[fbA + padi(nn)];
+      const T2 x = sm[fbA + padi<LOGE>(nn)];
 #pragma unroll
       for (int f = 0; f < NF; ++f) v[f][r] = (TPT == 1 ? half : f) ? cmul(x, ldro(&tw[nn])) : x;
     }
 #pragma unroll
-    for (int f = 0; f < NF; ++f) dft_reg<16, false>(v[f]);
+    for (int f = 0; f < NF; ++f) dft_reg<(1 << LOGE), false>(v[f]);
     __syncthreads();
 #pragma unroll
     for (int f = 0; f < NF; ++f)
 #pragma unroll
-      for (int r = 0; r < 16; ++r) sm[fb[f] + padi((j << 4) + r)] = v[f][r];
+      for (int r = 0; r < (1 << LOGE); ++r) sm[fb[f] + padi<LOGE>((j << LOGE) + r)] = v[f][r];
     __syncthreads();
   }
-  const int np = fft_npass(a.logH);
-  smem_passes<false, NF>(sm, fb, j, tpf, a.logH, 1, np - 1, 4, tw, a.logP, Identity{});
+  const int np = fft_npass<LOGE>(a.logH);
+  smem_passes<false, NF, LOGE>(sm, fb, j, tpf, a.logH, 1, np - 1, LOGE, tw, a.logP, Identity{});
   int logNs = 0;
-  for (int p = 0; p < np - 1; ++p) logNs += fft_logr(p, a.logH);
+  for (int p = 0; p < np - 1; ++p) logNs += fft_logr<LOGE>(p, a.logH);
   // last pass: X[2k + half] straight to the tiled intermediate
   T2* out = static_cast<T2*>(a.inter) + (size_t)c * P * a.nrows;
-  last_pass_dispatch<false, NF>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int k, const T2 (&v)[NF]) {
+  last_pass_dispatch<false, NF, LOGE>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int k, const T2 (&v)[NF]) {
     if (!live) return;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -158,18 +161,18 @@ __device__ __forceinline__ T2 recombine(const T2 (&v)[TPT], int half, const T2* 
   }
 }
 
-// CTA: 2^log_cols consecutive columns of one channel; (3 - TPT) * H/16 threads per column.
+// CTA: 2^log_cols consecutive columns of one channel; (3 - TPT) * H/E threads per column.
 // Lane order puts the columns of a tile that the CTA holds (min(2^log_cols, W) of them) in
 // adjacent lanes (lane pairs when TPT = 1), so with a whole tile per CTA the global loads and
 // stores of a warp are whole 32-byte sectors; with fewer columns per CTA the CTAs of the
 // neighbouring columns read the rest of each sector, through L2.
-template <typename CT, int TPT>
-__global__ void __launch_bounds__(LaunchMax<CT, TPT>::value) k_col_conv(ColArgs a) {
+template <typename CT, int TPT, int LOGE>
+__global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_col_conv(ColArgs a) {
   using T2 = CT;
   constexpr int W = GridT<CT>::W, NF = TPT, LPT = 3 - TPT;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
-  const int H = 1 << a.logH, P = 1 << a.logP, tpf = H >> 4, HS = padded_len(H);
+  const int H = 1 << a.logH, P = 1 << a.logP, tpf = H >> LOGE, HS = padded_len<LOGE>(H);
   const int cw = min(1 << a.log_cols, W);               // columns side by side in the lanes
   const int per_grp = LPT * cw * tpf;
   const int g = threadIdx.x / per_grp, rem = threadIdx.x - g * per_grp;
@@ -186,12 +189,12 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT>::value) k_col_conv(ColArgs 
   const T2* tw = static_cast<const T2*>(a.tw);
   T2* blk = static_cast<T2*>(a.inter) + (size_t)c * P * a.nrows + (size_t)tile * a.nrows * W;
   const int row_hi = a.row_lo + a.nrows - 1;
-  // pass 0 from global: a[n] and/or a[n] w^n, n = j + 16-stride
+  // pass 0 from global: a[n] and/or a[n] w^n, n = j + (H/E)-stride
   {
-    const int lognb = a.logH - 4;
-    T2 v[NF][16];
+    const int lognb = a.logH - LOGE;
+    T2 v[NF][1 << LOGE];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
+    for (int r = 0; r < (1 << LOGE); ++r) {
       const int nn = j + (r << lognb);
       const T2 x = (nn >= a.row_lo && nn <= row_hi) ? blk[(nn - a.row_lo) * W + w] : czero<T2>();
 #pragma unroll
@@ -199,18 +202,18 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT>::value) k_col_conv(ColArgs 
     }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      dft_reg<16, false>(v[f]);
+      dft_reg<(1 << LOGE), false>(v[f]);
 #pragma unroll
-      for (int r = 0; r < 16; ++r) sm[fb[f] + padi((j << 4) + r)] = v[f][r];
+      for (int r = 0; r < (1 << LOGE); ++r) sm[fb[f] + padi<LOGE>((j << LOGE) + r)] = v[f][r];
     }
     __syncthreads();
   }
-  const int np = fft_npass(a.logH);
+  const int np = fft_npass<LOGE>(a.logH);
   // remaining forward passes but the last
-  smem_passes<false, NF>(sm, fb, j, tpf, a.logH, 1, np - 1, 4, tw, a.logP, Identity{});
+  smem_passes<false, NF, LOGE>(sm, fb, j, tpf, a.logH, 1, np - 1, LOGE, tw, a.logP, Identity{});
   // last forward pass, product with the spectrum column, first inverse pass (same radix), in
-  // registers; the inverse then runs its radix-16 passes
-  const int lr0 = fft_logr(np - 1, a.logH);
+  // registers; the inverse then runs its radix-E passes
+  const int lr0 = fft_logr<LOGE>(np - 1, a.logH);
   {
     const int qq = min(qcol, P - qcol);
     const T2* col = static_cast<const T2*>(a.spec) + (size_t)qq * (H + 1);
@@ -220,17 +223,12 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT>::value) k_col_conv(ColArgs 
       const T2 s = odd ? ldro(&col[half_h + 1 + min(k, H - 1 - k)]) : ldro(&col[min(k, H - k)]);
       return cmul(v, s);
     };
-    switch (lr0) {
-      case 4: conv_mid_pass<4, NF>(sm, fb, j, tpf, a.logH, tw, a.logP, spec_mul); break;
-      case 3: conv_mid_pass<3, NF>(sm, fb, j, tpf, a.logH, tw, a.logP, spec_mul); break;
-      case 2: conv_mid_pass<2, NF>(sm, fb, j, tpf, a.logH, tw, a.logP, spec_mul); break;
-      default: conv_mid_pass<1, NF>(sm, fb, j, tpf, a.logH, tw, a.logP, spec_mul); break;
-    }
+    conv_mid_dispatch<NF, LOGE>(lr0, sm, fb, j, tpf, a.logH, tw, a.logP, spec_mul);
   }
   for (int p = 1; p < np - 1; ++p)
-    smem_pass<4, true, NF>(sm, fb, j, tpf, a.logH, lr0 + 4 * (p - 1), tw, a.logP, Identity{});
-  // last inverse pass (radix 16, Ns = H/16) recombines y[n] = A[n] + conj(w^n) B[n] for kept rows
-  last_pass<4, true, NF>(sm, fb, j, tpf, a.logH, a.logH - 4, tw, a.logP, [&](int nn, const T2 (&v)[NF]) {
+    smem_pass<LOGE, true, NF, LOGE>(sm, fb, j, tpf, a.logH, lr0 + LOGE * (p - 1), tw, a.logP, Identity{});
+  // last inverse pass (radix E, Ns = H/E) recombines y[n] = A[n] + conj(w^n) B[n] for kept rows
+  last_pass<LOGE, true, NF, LOGE>(sm, fb, j, tpf, a.logH, a.logH - LOGE, tw, a.logP, [&](int nn, const T2 (&v)[NF]) {
     const T2 y = recombine<TPT>(v, half, tw, nn);
     if (!half && nn >= a.row_lo && nn <= row_hi) blk[(nn - a.row_lo) * W + w] = y;
   });
@@ -253,14 +251,14 @@ struct RowInvArgs {
   int rows_per_cta;
 };
 
-template <typename CT, int TPT>
-__global__ void __launch_bounds__(LaunchMax<CT, TPT>::value) k_row_inv(RowInvArgs a) {
+template <typename CT, int TPT, int LOGE>
+__global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_inv(RowInvArgs a) {
   using T2 = CT;
   using VT = typename GridT<CT>::VT;
   constexpr int W = GridT<CT>::W, NF = TPT, LPT = 3 - TPT;
   extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
-  const int H = 1 << a.logH, P = 1 << a.logP, tpf = H >> 4, HS = padded_len(H);
+  const int H = 1 << a.logH, P = 1 << a.logP, tpf = H >> LOGE, HS = padded_len<LOGE>(H);
   const int per_row = LPT * tpf;
   const int g = threadIdx.x / per_row, rem = threadIdx.x - g * per_row;
   const int half = TPT == 1 ? (rem & 1) : 0, j = TPT == 1 ? (rem >> 1) : rem;
@@ -274,12 +272,12 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT>::value) k_row_inv(RowInvArg
 #pragma unroll
   for (int f = 0; f < NF; ++f) fb[f] = (2 * g + (TPT == 1 ? half : f)) * HS;
   const T2* blk = static_cast<const T2*>(a.inter) + (size_t)c * P * a.nrows;
-  // pass 0 (inverse, radix 16, Ns = 1) from global: Y[2k] and/or Y[2k+1]
+  // pass 0 (inverse, radix E, Ns = 1) from global: Y[2k] and/or Y[2k+1]
   {
-    const int lognb = a.logH - 4;
-    T2 v[NF][16];
+    const int lognb = a.logH - LOGE;
+    T2 v[NF][1 << LOGE];
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
+    for (int r = 0; r < (1 << LOGE); ++r) {
 #pragma unroll
       for (int f = 0; f < NF; ++f) {
         const int q = 2 * (j + (r << lognb)) + (TPT == 1 ? half : f);
@@ -288,50 +286,50 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT>::value) k_row_inv(RowInvArg
     }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      dft_reg<16, true>(v[f]);
+      dft_reg<(1 << LOGE), true>(v[f]);
 #pragma unroll
-      for (int r = 0; r < 16; ++r) sm[fb[f] + padi((j << 4) + r)] = v[f][r];
+      for (int r = 0; r < (1 << LOGE); ++r) sm[fb[f] + padi<LOGE>((j << LOGE) + r)] = v[f][r];
     }
     __syncthreads();
   }
-  const int np = fft_npass(a.logH);
-  smem_passes<true, NF>(sm, fb, j, tpf, a.logH, 1, np - 1, 4, tw, a.logP, Identity{});
+  const int np = fft_npass<LOGE>(a.logH);
+  smem_passes<true, NF, LOGE>(sm, fb, j, tpf, a.logH, 1, np - 1, LOGE, tw, a.logP, Identity{});
   int logNs = 0;
-  for (int p = 0; p < np - 1; ++p) logNs += fft_logr(p, a.logH);
+  for (int p = 0; p < np - 1; ++p) logNs += fft_logr<LOGE>(p, a.logH);
   const double sc = a.scale;
   if (a.dense) {
     double2* out = a.dense_out + (size_t)c * a.m * a.m + (size_t)iy * a.m;
-    last_pass_dispatch<true, NF>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int nn, const T2 (&v)[NF]) {
+    last_pass_dispatch<true, NF, LOGE>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int nn, const T2 (&v)[NF]) {
       const T2 y = recombine<TPT>(v, half, tw, nn);
       if (!half && live && nn < a.m) out[nn] = cto_d2(y, sc);
     });
     return;
   }
   // sparse mode: results into registers, then through shared memory to the active points
-  T2 ybuf[16];
+  T2 ybuf[1 << LOGE];
   int ycnt = 0;
-  last_pass_dispatch<true, NF>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int nn, const T2 (&v)[NF]) {
-    ybuf[ycnt++ & 15] = recombine<TPT>(v, half, tw, nn);
+  last_pass_dispatch<true, NF, LOGE>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int nn, const T2 (&v)[NF]) {
+    ybuf[ycnt++ & ((1 << LOGE) - 1)] = recombine<TPT>(v, half, tw, nn);
   });
   __syncthreads();
   if (!half) {
     // replay the output indices of the last pass to place the recombined values
-    const int lr = fft_logr(np - 1, a.logH);
-    const int R = 1 << lr, NB = 16 >> lr;
+    const int lr = fft_logr<LOGE>(np - 1, a.logH);
+    const int R = 1 << lr, NB = (1 << LOGE) >> lr;
     const int nsm = (1 << logNs) - 1;
     int q = 0;
     for (int t = 0; t < NB; ++t) {
       const int b = j + t * tpf;
       const int k = b & nsm;
       const int base = ((b - k) << lr) + k;
-      for (int r = 0; r < R; ++r) sm[fbA + padi(base + (r << logNs))] = ybuf[q++];
+      for (int r = 0; r < R; ++r) sm[fbA + padi<LOGE>(base + (r << logNs))] = ybuf[q++];
     }
   }
   __syncthreads();
   if (live) {
     VT* out = static_cast<VT*>(a.vact) + (size_t)c * a.n_act;
     const int a1 = a.row_ptr[iy + 1];
-    for (int ap = a.row_ptr[iy] + rem; ap < a1; ap += per_row) out[ap] = cto_vt(sm[fbA + padi(a.act_ix[ap])], sc);
+    for (int ap = a.row_ptr[iy] + rem; ap < a1; ap += per_row) out[ap] = cto_vt(sm[fbA + padi<LOGE>(a.act_ix[ap])], sc);
   }
 }
 
@@ -438,26 +436,6 @@ __global__ void k_gather(GatherArgs a) {
   }
 }
 
-__global__ void k_gram_inv(const double* __restrict__ gi, int blo, int cnt, int n, int nrhs,
-                           const double2* __restrict__ x, double2* __restrict__ y) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n * nrhs) return;
-  const int r = t / n, i = t - r * n;
-  const double* row = gi + (size_t)i * cnt;
-  const double2* xv = x + (size_t)r * n;
-  double re = 0.0, im = 0.0;
-  int j = i - blo;
-  if (j < 0) j += n;
-  for (int d = 0; d < cnt; ++d) {
-    const double g = row[d];
-    const double2 xx = xv[j];
-    re = fma(g, xx.x, re);
-    im = fma(g, xx.y, im);
-    if (++j == n) j = 0;
-  }
-  y[t] = double2{re, im};
-}
-
 // ------------------------------------------------------------------------------------
 // launch configuration
 // ------------------------------------------------------------------------------------
@@ -467,11 +445,6 @@ static aim_status ensure_smem(K kernel, size_t bytes) {
     AIM_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
   }
   return AIM_OK;
-}
-
-size_t inter_bytes_needed(const aim_ctx* ctx, int channels, int precision) {
-  const size_t el = precision == AIM_MIXED ? sizeof(float2) : sizeof(double2);   // dfc is 16 bytes too
-  return (size_t)channels * ctx->P * ctx->nrows * el;
 }
 
 // tables of the context in the element type of the grid product
@@ -490,48 +463,62 @@ static int precision_of(dfc*) { return AIM_FP64; }
 
 constexpr size_t kMaxDynSmem = 227 * 1024;   // opt-in dynamic shared memory per CTA
 
+// Which (transforms per thread, elements per thread) pairs are compiled for an element type:
+// native binary64 keeps two transforms of 16 elements per thread
+template <typename CT, int TPT, int LOGE>
+struct Supports {
+  static constexpr bool value = std::is_same<CT, double2>::value ? (TPT == 2 && LOGE == 4) : true;
+};
+
+inline int loge_of(const Schedule& sc) { return sc.elems == 8 ? 3 : 4; }
+
 // columns per column-pass CTA: the schedule's choice, else the fewest whole tiles of W
 // columns that give at least 128 threads
-template <typename CT, int TPT>
+template <typename CT, int TPT, int LOGE>
 static int col_cols_of(const Schedule& sc, int logH, int logP) {
   constexpr int W = GridT<CT>::W, LPT = 3 - TPT;
   if (sc.col_cols > 0) return sc.col_cols;
-  const int tpf = (1 << logH) / 16, ntiles = (1 << logP) / W;
+  const int tpf = (1 << logH) >> LOGE, ntiles = (1 << logP) / W;
   int tpc = 1;
   while (tpc * LPT * W * tpf < 128 && tpc < ntiles) tpc *= 2;
   return tpc * W;
 }
 
-template <typename CT, int TPT>
+template <typename CT, int TPT, int LOGE>
 static bool feasible_tpt(const Schedule& sc, int logH, int logP) {
-  constexpr int LPT = 3 - TPT;
-  const int H = 1 << logH, tpf = H / 16, cols = col_cols_of<CT, TPT>(sc, logH, logP);
-  if (cols < 1 || (cols & (cols - 1)) || cols > (1 << logP)) return false;
-  if (LPT * cols * tpf > LaunchMax<CT, TPT>::value || LPT * cols * tpf < 32) return false;
-  if (2 * (size_t)cols * padded_len(H) * sizeof(CT) > kMaxDynSmem) return false;
-  if (sc.min_row_threads < 32 || sc.min_row_threads > 1024) return false;
-  // row passes: one row per CTA must fit too
-  if (2 * (size_t)padded_len(H) * sizeof(CT) > kMaxDynSmem || LPT * tpf > LaunchMax<CT, TPT>::value) return false;
-  return true;
-}
-
-bool schedule_feasible(int precision, int logH, int logP, const Schedule& s) {
-  if (s.tpt != 1 && s.tpt != 2) return false;
-  switch (precision) {
-    case AIM_MIXED: return s.tpt == 1 ? feasible_tpt<float2, 1>(s, logH, logP) : feasible_tpt<float2, 2>(s, logH, logP);
-    case AIM_FP64: return s.tpt == 1 ? feasible_tpt<dfc, 1>(s, logH, logP) : feasible_tpt<dfc, 2>(s, logH, logP);
-    case AIM_FP64_NATIVE: return s.tpt == 2 && feasible_tpt<double2, 2>(s, logH, logP);
-    default: return false;
+  if constexpr (!Supports<CT, TPT, LOGE>::value) {
+    return false;
+  } else {
+    constexpr int LPT = 3 - TPT;
+    if (logH < LOGE + 1) return false;   // at least two passes
+    const int H = 1 << logH, tpf = H >> LOGE, cols = col_cols_of<CT, TPT, LOGE>(sc, logH, logP);
+    if (cols < 1 || (cols & (cols - 1)) || cols > (1 << logP)) return false;
+    if (LPT * cols * tpf > LaunchMax<CT, TPT, LOGE>::value || LPT * cols * tpf < 32) return false;
+    if (2 * (size_t)cols * padded_len<LOGE>(H) * sizeof(CT) > kMaxDynSmem) return false;
+    if (sc.min_row_threads < 32 || sc.min_row_threads > 1024) return false;
+    // row passes: one row per CTA must fit too
+    if (2 * (size_t)padded_len<LOGE>(H) * sizeof(CT) > kMaxDynSmem || LPT * tpf > LaunchMax<CT, TPT, LOGE>::value)
+      return false;
+    return true;
   }
 }
 
-template <typename CT, int TPT>
+template <typename CT>
+static bool feasible_for(const Schedule& s, int logH, int logP) {
+  if (s.tpt != 1 && s.tpt != 2) return false;
+  if (s.elems != 0 && s.elems != 8 && s.elems != 16) return false;
+  if (loge_of(s) == 3)
+    return s.tpt == 1 ? feasible_tpt<CT, 1, 3>(s, logH, logP) : feasible_tpt<CT, 2, 3>(s, logH, logP);
+  return s.tpt == 1 ? feasible_tpt<CT, 1, 4>(s, logH, logP) : feasible_tpt<CT, 2, 4>(s, logH, logP);
+}
+
+template <typename CT, int TPT, int LOGE>
 static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdArgs fa, RowInvArgs ia,
                              const Schedule& sc, cudaStream_t st) {
   const int min_row_threads = sc.min_row_threads;
   using T2 = CT;
   constexpr int LPT = 3 - TPT;
-  const int H = ctx->H, tpf = H / 16, HS = padded_len(H);
+  const int H = ctx->H, tpf = H >> LOGE, HS = padded_len<LOGE>(H);
   const void* tw = twiddles(ctx, (CT*)nullptr);
   const void* spec = spectrum(ctx, filtered, (CT*)nullptr);
 
@@ -540,7 +527,7 @@ static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdAr
   // last one load zeros and store nothing), within the launch bound
   int rpc = 1;
   while (((rpc * LPT * tpf < min_row_threads && rpc < ctx->nrows) || rpc * LPT * tpf < 32) &&
-         2 * rpc * LPT * tpf <= LaunchMax<CT, TPT>::value)
+         2 * rpc * LPT * tpf <= LaunchMax<CT, TPT, LOGE>::value)
     rpc *= 2;
   const int row_blocks = (ctx->nrows + rpc - 1) / rpc;
   const size_t sm_row = 2 * (size_t)rpc * HS * sizeof(T2);
@@ -552,15 +539,15 @@ static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdAr
   fa.nrows = ctx->nrows;
   fa.inter = ctx->inter;
   fa.rows_per_cta = rpc;
-  AIM_TRY(ensure_smem(k_row_fwd<CT, TPT>, sm_row));
+  AIM_TRY(ensure_smem(k_row_fwd<CT, TPT, LOGE>, sm_row));
   {
     ProfScope ps(K_ROW_FWD, st);
-    k_row_fwd<CT, TPT><<<dim3(row_blocks, channels), rpc * LPT * tpf, sm_row, st>>>(fa);
+    k_row_fwd<CT, TPT, LOGE><<<dim3(row_blocks, channels), rpc * LPT * tpf, sm_row, st>>>(fa);
   }
   AIM_CUDA_TRY(cudaGetLastError());
 
   // column pass
-  const int cols = col_cols_of<CT, TPT>(sc, ctx->logH, ctx->logP);
+  const int cols = col_cols_of<CT, TPT, LOGE>(sc, ctx->logH, ctx->logP);
   int log_cols = 0;
   while ((1 << log_cols) < cols) ++log_cols;
   ColArgs ca;
@@ -573,10 +560,10 @@ static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdAr
   ca.nrows = ctx->nrows;
   ca.log_cols = log_cols;
   const size_t sm_col = 2 * (size_t)cols * HS * sizeof(T2);
-  AIM_TRY(ensure_smem(k_col_conv<CT, TPT>, sm_col));
+  AIM_TRY(ensure_smem(k_col_conv<CT, TPT, LOGE>, sm_col));
   {
     ProfScope ps(K_COL_CONV, st);
-    k_col_conv<CT, TPT><<<dim3(ctx->P / cols, channels), cols * LPT * tpf, sm_col, st>>>(ca);
+    k_col_conv<CT, TPT, LOGE><<<dim3(ctx->P / cols, channels), cols * LPT * tpf, sm_col, st>>>(ca);
   }
   AIM_CUDA_TRY(cudaGetLastError());
 
@@ -589,10 +576,10 @@ static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdAr
   ia.nrows = ctx->nrows;
   ia.scale = 1.0 / ((double)ctx->P * (double)ctx->P);
   ia.rows_per_cta = rpc;
-  AIM_TRY(ensure_smem(k_row_inv<CT, TPT>, sm_row));
+  AIM_TRY(ensure_smem(k_row_inv<CT, TPT, LOGE>, sm_row));
   {
     ProfScope ps(K_ROW_INV, st);
-    k_row_inv<CT, TPT><<<dim3(row_blocks, channels), rpc * LPT * tpf, sm_row, st>>>(ia);
+    k_row_inv<CT, TPT, LOGE><<<dim3(row_blocks, channels), rpc * LPT * tpf, sm_row, st>>>(ia);
   }
   AIM_CUDA_TRY(cudaGetLastError());
   return AIM_OK;
@@ -605,12 +592,16 @@ static aim_status launch_three_passes(aim_ctx* ctx, int channels, bool filtered,
   if (ctx->H < 32) return fail(AIM_EINVAL, "embedding side P must be >= 64");
   const int p = precision_of((CT*)nullptr);
   const Schedule sc = ctx->sched[p];
-  if (!schedule_feasible(p, ctx->logH, ctx->logP, sc)) return fail(AIM_EINVAL, "launch schedule not feasible");
+  if (!feasible_for<CT>(sc, ctx->logH, ctx->logP)) return fail(AIM_EINVAL, "launch schedule not feasible");
   if constexpr (std::is_same<CT, double2>::value) {
-    return launch_tpt<CT, 2>(ctx, channels, filtered, fa, ia, sc, st);
+    return launch_tpt<CT, 2, 4>(ctx, channels, filtered, fa, ia, sc, st);
   } else {
-    if (sc.tpt == 1) return launch_tpt<CT, 1>(ctx, channels, filtered, fa, ia, sc, st);
-    return launch_tpt<CT, 2>(ctx, channels, filtered, fa, ia, sc, st);
+    if (loge_of(sc) == 3) {
+      if (sc.tpt == 1) return launch_tpt<CT, 1, 3>(ctx, channels, filtered, fa, ia, sc, st);
+      return launch_tpt<CT, 2, 3>(ctx, channels, filtered, fa, ia, sc, st);
+    }
+    if (sc.tpt == 1) return launch_tpt<CT, 1, 4>(ctx, channels, filtered, fa, ia, sc, st);
+    return launch_tpt<CT, 2, 4>(ctx, channels, filtered, fa, ia, sc, st);
   }
 }
 
@@ -701,25 +692,5 @@ aim_status grid_product_dense(aim_ctx* ctx, bool filtered, int nrhs, const doubl
   ia.n_act = ctx->n_act;
   return launch_three_passes<CT>(ctx, nrhs, filtered, fa, ia, st);
 }
-
-aim_status gram_inv_apply(aim_ctx* ctx, int nrhs, const double2* x, double2* y, cudaStream_t st) {
-  if (ctx->gram_inv == nullptr) return fail(AIM_ESTATE, "no Gram matrix on a TM context");
-  const int blo = ctx->gram_band;
-  const int cnt = (blo * 2 + 1 <= ctx->n) ? 2 * blo + 1 : ctx->n;
-  const int total = ctx->n * nrhs;
-  {
-    ProfScope ps(K_GRAM, st);
-    k_gram_inv<<<(total + 255) / 256, 256, 0, st>>>(ctx->gram_inv, blo, cnt, ctx->n, nrhs, x, y);
-  }
-  AIM_CUDA_TRY(cudaGetLastError());
-  return AIM_OK;
-}
-
-template aim_status grid_pass<double2>(aim_ctx*, const PassSpec&, int, const double2*, double2*, cudaStream_t);
-template aim_status grid_pass<float2>(aim_ctx*, const PassSpec&, int, const double2*, double2*, cudaStream_t);
-template aim_status grid_pass<dfc>(aim_ctx*, const PassSpec&, int, const double2*, double2*, cudaStream_t);
-template aim_status grid_product_dense<double2>(aim_ctx*, bool, int, const double2*, double2*, cudaStream_t);
-template aim_status grid_product_dense<float2>(aim_ctx*, bool, int, const double2*, double2*, cudaStream_t);
-template aim_status grid_product_dense<dfc>(aim_ctx*, bool, int, const double2*, double2*, cudaStream_t);
 
 }  // namespace aim

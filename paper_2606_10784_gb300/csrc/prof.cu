@@ -20,7 +20,7 @@ static const char* kKernelNames[K_COUNT] = {
     "setup_segment_pairs",
     "setup_near_entries",
     "rhs_planewave",
-    "gmres_blas",
+    "gmres_arnoldi (CGS2 projections, norm, normalisation; timed per step)",
 };
 
 namespace {
@@ -42,8 +42,8 @@ bool profiling_active() {
   return g_timing;
 }
 
-ProfScope::ProfScope(int id_, cudaStream_t st_) : id(id_), st(st_), slot(-1) {
-  g_launches[id].fetch_add(1, std::memory_order_relaxed);
+ProfScope::ProfScope(int id_, cudaStream_t st_, bool count_launch) : id(id_), st(st_), slot(-1) {
+  if (count_launch) g_launches[id].fetch_add(1, std::memory_order_relaxed);
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_timing) return;
   if (g_used == g_pool.size()) {

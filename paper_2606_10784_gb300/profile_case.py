@@ -10,7 +10,7 @@ k_col_conv launch is the operator's first column pass (3 channels for N, 1 for S
 
 --time prints the mean device time per launch of each grid kernel (CUDA events on the launching
 stream, after one warm-up product). --sweep does that for every feasible launch schedule.
---schedule tpt,row_threads,col_cols fixes one schedule.
+--schedule tpt,row_threads,col_cols[,elems_per_thread] fixes one schedule.
 """
 from __future__ import annotations
 
@@ -56,18 +56,19 @@ def main(argv=None):
     x = torch.from_numpy(synth.random_coeffs(wl.n, args.nrhs, 0)).cuda()
     y = torch.empty_like(x)
     if args.schedule:
-        t, r, c = (int(v) for v in args.schedule.split(","))
-        ctx.set_schedule(prec, t, r, c)
+        vals = [int(v) for v in args.schedule.split(",")]
+        ctx.set_schedule(prec, *vals)
     if args.sweep:
-        for t in (1, 2):
-            for r in (128, 256):
-                for c in (0, 1, 2, 4, 8):
-                    try:
-                        ctx.set_schedule(prec, t, r, c)
-                    except aim.AimError:
-                        continue
-                    ms = _timed(aim, ctx, args.op, x, y, prec, max(args.repeat, 1))
-                    print(json.dumps({"schedule": ctx.get_schedule(prec), "ms_per_launch": ms}))
+        for e in (16, 8):
+            for t in (1, 2):
+                for r in (128, 256):
+                    for c in (0, 1, 2, 4, 8):
+                        try:
+                            ctx.set_schedule(prec, t, r, c, e)
+                        except aim.AimError:
+                            continue
+                        ms = _timed(aim, ctx, args.op, x, y, prec, max(args.repeat, 1))
+                        print(json.dumps({"schedule": ctx.get_schedule(prec), "ms_per_launch": ms}))
     elif args.time:
         ms = _timed(aim, ctx, args.op, x, y, prec, max(args.repeat, 1))
         print(json.dumps({"schedule": ctx.get_schedule(prec), "ms_per_launch": ms}))
