@@ -7,12 +7,19 @@
 // Mixed precision: the outer loop computes r = b - A x with the FP64 grid product, an inner
 // GMRES with the FP32 grid product solves A d = r to a looser tolerance, and x += d, until
 // the FP64 residual meets the target (iterative refinement).
+//
+// The Krylov basis is stored in double-float (hi + lo floats per real, 16 bytes per complex like
+// complex128) and the Gram-Schmidt projections V^H w and updates w - V h run their products and
+// per-thread sums in double-float arithmetic on the FP32 pipe, with FP64 only for the block
+// reductions and the chunk sums. In binary64 they would be bound by GB300's FP64 rate (16 FP64
+// operations per basis element and iteration, about 3x the time of their HBM traffic).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
 
 #include "aim_internal.h"
+#include "dfloat.cuh"
 
 namespace aim {
 
@@ -101,29 +108,106 @@ __global__ void k_multidot_finish(const double2* __restrict__ part, int nz, int 
   out[t] = double2{re, im};
 }
 
-// Stage 1 of out[r][i] += sign * sum_j V[j][r][i] c[j*nrhs + r], parallel over chunks of kCgsChunk
-// Krylov vectors: part[chunk][r][i] = sum over the chunk. Stage 2 adds the chunk partial sums in
+// Basis updates out[r][i] += sign * sum_j V[j][r][i] c[j*nrhs + r] run over chunks of kCgsChunk
+// Krylov vectors: stage 1 (k_vcombine_partial_df) sums each chunk, stage 2 adds the chunk sums in
 // chunk order, so the result does not depend on scheduling.
 constexpr int kCgsChunk = 32;
 
-__global__ void k_vcombine_partial(const double2* __restrict__ V, const double2* __restrict__ c, int J, int n, int nrhs,
-                                   double2* __restrict__ part) {
+__device__ __forceinline__ dfc to_dfc(double2 d) {
+  dfc r;
+  df_split(d.x, r.xh, r.xl);
+  df_split(d.y, r.yh, r.yl);
+  return r;
+}
+__device__ __forceinline__ double2 to_d2(float h_re, float l_re, float h_im, float l_im) {
+  return double2{(double)h_re + (double)l_re, (double)h_im + (double)l_im};
+}
+
+__global__ void k_to_dfc(const double2* __restrict__ src, int count, dfc* __restrict__ dst) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < count) dst[t] = to_dfc(src[t]);
+}
+
+// Double-float form of k_multidot_partial: part[(z J + j) nrhs + r] = sum over chunk z of
+// conj(V[j][r][i]) w[r][i], products and per-thread sums in double-float, block sum in FP64.
+__global__ void k_multidot_partial_df(const dfc* __restrict__ V, const dfc* __restrict__ w, int n, int nrhs, int J,
+                                      double2* __restrict__ part) {
+  const int j = blockIdx.x, r = blockIdx.y, z = blockIdx.z;
+  const int i0 = z * kDotChunk, i1 = min(n, i0 + kDotChunk);
+  const dfc* v = V + ((size_t)j * nrhs + r) * n;
+  const dfc* x = w + (size_t)r * n;
+  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const dfc a = v[i], b = x[i];
+    float ph, pl;
+    df_dot2<+1>(a.xh, a.xl, b.xh, b.xl, a.yh, a.yl, b.yh, b.yl, ph, pl);   // ax bx + ay by
+    df_add(rh, rl, ph, pl, rh, rl);
+    df_dot2<-1>(a.xh, a.xl, b.yh, b.yl, a.yh, a.yl, b.xh, b.xl, ph, pl);   // ax by - ay bx
+    df_add(ih, il, ph, pl, ih, il);
+  }
+  const double2 acc = to_d2(rh, rl, ih, il);
+  double re = acc.x, im = acc.y;
+  __shared__ double sre[32], sim[32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, off);
+    im += __shfl_xor_sync(0xffffffffu, im, off);
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sre[wid] = re; sim[wid] = im; }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    re = lane < nw ? sre[lane] : 0.0;
+    im = lane < nw ? sim[lane] : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      re += __shfl_xor_sync(0xffffffffu, re, off);
+      im += __shfl_xor_sync(0xffffffffu, im, off);
+    }
+    if (lane == 0) part[((size_t)z * J + j) * nrhs + r] = double2{re, im};
+  }
+}
+
+// out[t] = sum of the chunk partials (FP64, in chunk order), and its double-float copy
+__global__ void k_multidot_finish_df(const double2* __restrict__ part, int nz, int count, double2* __restrict__ out,
+                                     dfc* __restrict__ out_df) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  double re = 0.0, im = 0.0;
+  for (int z = 0; z < nz; ++z) {
+    const double2 p = part[(size_t)z * count + t];
+    re += p.x;
+    im += p.y;
+  }
+  out[t] = double2{re, im};
+  out_df[t] = to_dfc(double2{re, im});
+}
+
+// Stage 1 of the basis update: part[chunk][r][i] = sum over the chunk of V[j][r][i] c[j*nrhs + r]
+__global__ void k_vcombine_partial_df(const dfc* __restrict__ V, const dfc* __restrict__ c, int J, int n, int nrhs,
+                                      double2* __restrict__ part) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int chunk = blockIdx.y, r = blockIdx.z;
   if (i >= n) return;
   const int j0 = chunk * kCgsChunk, j1 = min(J, j0 + kCgsChunk);
-  double re = 0.0, im = 0.0;
+  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
   for (int j = j0; j < j1; ++j) {
-    const double2 v = V[((size_t)j * nrhs + r) * n + i];
-    const double2 h = c[(size_t)j * nrhs + r];
-    re += v.x * h.x - v.y * h.y;
-    im += v.x * h.y + v.y * h.x;
+    const dfc v = V[((size_t)j * nrhs + r) * n + i];
+    const dfc h = c[(size_t)j * nrhs + r];
+    float ph, pl;
+    df_dot2<-1>(v.xh, v.xl, h.xh, h.xl, v.yh, v.yl, h.yh, h.yl, ph, pl);   // vx hx - vy hy
+    df_add(rh, rl, ph, pl, rh, rl);
+    df_dot2<+1>(v.xh, v.xl, h.yh, h.yl, v.yh, v.yl, h.xh, h.xl, ph, pl);   // vx hy + vy hx
+    df_add(ih, il, ph, pl, ih, il);
   }
-  part[((size_t)chunk * nrhs + r) * n + i] = double2{re, im};
+  part[((size_t)chunk * nrhs + r) * n + i] = to_d2(rh, rl, ih, il);
 }
 
-__global__ void k_vcombine_finish(const double2* __restrict__ part, int nchunks, int n, int nrhs, double sign,
-                                  double2* __restrict__ out) {
+// Stage 2: out += sign * sum of the chunk partials (FP64, in chunk order); out_df (may be null)
+// receives the double-float copy of the updated out
+__global__ void k_vcombine_finish_df(const double2* __restrict__ part, int nchunks, int n, int nrhs, double sign,
+                                     double2* __restrict__ out, dfc* __restrict__ out_df) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * nrhs) return;
   double re = 0.0, im = 0.0;
@@ -132,8 +216,9 @@ __global__ void k_vcombine_finish(const double2* __restrict__ part, int nchunks,
     re += p.x;
     im += p.y;
   }
-  out[t].x += sign * re;
-  out[t].y += sign * im;
+  const double2 o = double2{out[t].x + sign * re, out[t].y + sign * im};
+  out[t] = o;
+  if (out_df != nullptr) out_df[t] = to_dfc(o);
 }
 
 __global__ void k_add_small(double2* a, const double2* b, int count) {
@@ -141,15 +226,18 @@ __global__ void k_add_small(double2* a, const double2* b, int count) {
   if (t < count) { a[t].x += b[t].x; a[t].y += b[t].y; }
 }
 
-// dst[r] = w[r] / sqrt(nrm2[r].x) (zero if the norm vanished); active[r] == 0 zeroes dst[r]
+// v = w[r] / sqrt(nrm2[r].x) (zero if the norm vanished, or active[r] == 0): the new basis
+// vector in double-float (dst) and in binary64 (cur, the next matrix-vector product's input)
 __global__ void k_normalize(const double2* __restrict__ w, const double2* __restrict__ nrm2, const int* __restrict__ active,
-                            int n, int nrhs, double2* __restrict__ dst) {
+                            int n, int nrhs, dfc* __restrict__ dst, double2* __restrict__ cur) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * nrhs) return;
   const int r = t / n;
   const double nv = sqrt(fmax(nrm2[r].x, 0.0));
   const double s = (active[r] && nv > 0.0) ? 1.0 / nv : 0.0;
-  dst[t] = double2{w[t].x * s, w[t].y * s};
+  const double2 v = double2{w[t].x * s, w[t].y * s};
+  cur[t] = v;
+  dst[t] = to_dfc(v);
 }
 
 // r = b - Ax
@@ -173,7 +261,9 @@ inline Zc cconj(Zc a) { return {a.re, -a.im}; }
 inline double cabs2(Zc a) { return a.re * a.re + a.im * a.im; }
 
 struct Workspace {
-  double2 *V, *w, *r, *tmp, *dots, *dots2, *nrm;
+  dfc* V;                      // basis, double-float
+  double2 *w, *r, *cur, *tmp, *dots, *dots2, *nrm;
+  dfc *wdf, *dots_df, *dots2_df;
   int* active;
 };
 
@@ -209,22 +299,34 @@ aim_status dot_norms(const double2* vecs, int n, int nrhs, double2* out, double2
 
 }  // namespace
 
-// out += sign * V c over J Krylov vectors (two launches, deterministic order)
-static void vcombine(const double2* V, const double2* c, int J, int n, int nrhs, double sign, double2* out,
-                     double2* part, cudaStream_t st) {
+// out[j*nrhs + r] = <V[j][r], w[r]> for j < J over the double-float basis (two launches)
+static aim_status multidot_df(const dfc* V, const dfc* w, int J, int n, int nrhs, double2* out, dfc* out_df,
+                              double2* part, cudaStream_t st) {
+  const int nz = (n + kDotChunk - 1) / kDotChunk;
+  count_launches(K_GMRES, 2);
+  k_multidot_partial_df<<<dim3(J, nrhs, nz), 256, 0, st>>>(V, w, n, nrhs, J, part);
+  k_multidot_finish_df<<<blocks_for((long long)J * nrhs, 256), 256, 0, st>>>(part, nz, J * nrhs, out, out_df);
+  AIM_CUDA_TRY(cudaGetLastError());
+  return AIM_OK;
+}
+
+// out += sign * V c over J vectors of the double-float basis (two launches, deterministic order)
+static void vcombine_df(const dfc* V, const dfc* c, int J, int n, int nrhs, double sign, double2* out, dfc* out_df,
+                        double2* part, cudaStream_t st) {
   const int nch = (J + kCgsChunk - 1) / kCgsChunk;
   count_launches(K_GMRES, 2);
-  k_vcombine_partial<<<dim3((n + 255) / 256, nch, nrhs), 256, 0, st>>>(V, c, J, n, nrhs, part);
-  k_vcombine_finish<<<(n * nrhs + 255) / 256, 256, 0, st>>>(part, nch, n, nrhs, sign, out);
+  k_vcombine_partial_df<<<dim3((n + 255) / 256, nch, nrhs), 256, 0, st>>>(V, c, J, n, nrhs, part);
+  k_vcombine_finish_df<<<(n * nrhs + 255) / 256, 256, 0, st>>>(part, nch, n, nrhs, sign, out, out_df);
 }
 
 static aim_status ensure_krylov(aim_ctx* ctx, int nrhs, int restart) {
-  // basis (restart + 1), w, r, and the partial sums of vcombine (chunks of kCgsChunk vectors) or
-  // of multidot (chunks of kDotChunk elements), whichever needs more
+  // partial sums of the basis updates (chunks of kCgsChunk vectors) or of the inner products
+  // (chunks of kDotChunk elements), whichever needs more
   const size_t n = (size_t)ctx->n;
   const size_t nz = (n + kDotChunk - 1) / kDotChunk;
   const size_t part_vecs = std::max((size_t)(restart + kCgsChunk) / kCgsChunk, (nz * (restart + 1) + n - 1) / n);
-  const size_t nvec = (size_t)(restart + 1) + 2 + part_vecs;
+  // basis (restart + 1, double-float), w, r, the current vector, w in double-float, partial sums
+  const size_t nvec = (size_t)(restart + 1) + 4 + part_vecs;
   const size_t need = nvec * nrhs * ctx->n * sizeof(double2);
   if (ctx->kry_bytes < need) {
     if (ctx->kry) cudaFree(ctx->kry);
@@ -235,7 +337,8 @@ static aim_status ensure_krylov(aim_ctx* ctx, int nrhs, int restart) {
     ctx->kry = static_cast<double2*>(p);
     ctx->kry_bytes = need;
   }
-  const size_t rneed = ((size_t)(restart + 2) * 3 + 1) * nrhs * sizeof(double2) + nrhs * sizeof(int);
+  // dots, dots2, norms, their double-float copies, and the active flags
+  const size_t rneed = ((size_t)(restart + 2) * 5 + 1) * nrhs * sizeof(double2) + nrhs * sizeof(int);
   if (ctx->red_bytes < rneed) {
     if (ctx->red) cudaFree(ctx->red);
     if (ctx->red_host) cudaFreeHost(ctx->red_host);
@@ -266,16 +369,21 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
   const int n = ctx->n;
   const size_t vsz = (size_t)nrhs * n;
   AIM_TRY(ensure_krylov(ctx, nrhs, restart));
+  static_assert(sizeof(dfc) == sizeof(double2), "double-float complex must be 16 bytes");
   Workspace ws;
-  ws.V = ctx->kry;
-  ws.w = ws.V + (size_t)(restart + 1) * vsz;
+  ws.V = reinterpret_cast<dfc*>(ctx->kry);
+  ws.w = ctx->kry + (size_t)(restart + 1) * vsz;
   ws.r = ws.w + vsz;
-  ws.tmp = ws.r + vsz;
+  ws.cur = ws.r + vsz;
+  ws.wdf = reinterpret_cast<dfc*>(ws.cur + vsz);
+  ws.tmp = ws.cur + 2 * vsz;
   double2* red = reinterpret_cast<double2*>(ctx->red);
   ws.dots = red;                                   // (restart+1) * nrhs
   ws.dots2 = red + (size_t)(restart + 2) * nrhs;   // (restart+1) * nrhs
   ws.nrm = red + (size_t)(restart + 2) * 2 * nrhs; // nrhs
-  ws.active = reinterpret_cast<int*>(red + ((size_t)(restart + 2) * 3 + 1) * nrhs);
+  ws.dots_df = reinterpret_cast<dfc*>(red + (size_t)(restart + 2) * 3 * nrhs);   // (restart+1) * nrhs
+  ws.dots2_df = reinterpret_cast<dfc*>(red + (size_t)(restart + 2) * 4 * nrhs);  // (restart+1) * nrhs
+  ws.active = reinterpret_cast<int*>(red + ((size_t)(restart + 2) * 5 + 1) * nrhs);
   double2* hred = reinterpret_cast<double2*>(ctx->red_host);
   const int tpb = 256;
   const int nb = blocks_for((long long)vsz, tpb);
@@ -326,7 +434,7 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
 
     AIM_CUDA_TRY(cudaMemcpyAsync(ws.active, active.data(), nrhs * sizeof(int), cudaMemcpyHostToDevice, st));
     count_launches(K_GMRES, 1);
-    k_normalize<<<nb, tpb, 0, st>>>(ws.r, ws.nrm, ws.active, n, nrhs, ws.V);
+    k_normalize<<<nb, tpb, 0, st>>>(ws.r, ws.nrm, ws.active, n, nrhs, ws.V, ws.cur);
     AIM_CUDA_TRY(cudaGetLastError());
     for (int r = 0; r < nrhs; ++r) {
       g[(size_t)0 * nrhs + r] = {beta[r], 0.0};
@@ -339,20 +447,20 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
     // the next matvec on the device (one step of lookahead; the step queued after the last
     // useful one is discarded).
     auto arnoldi_step = [&](int j) -> aim_status {
-      double2* Vj = ws.V + (size_t)j * vsz;
       double2* slot = hred + (size_t)(j & 1) * (restart + 2) * nrhs;
-      AIM_TRY(apply_op(ctx, op, nrhs, Vj, ws.w, precision, st));
-      // CGS2 (2 launches here + 2 x 2 in multidot + 2 x 2 in vcombine + 2 in dot_norms), timed as
-      // one group when profiling
+      AIM_TRY(apply_op(ctx, op, nrhs, ws.cur, ws.w, precision, st));   // cur = v_j
+      // CGS2 (3 launches here + 2 x 2 in multidot_df + 2 x 2 in vcombine_df + 2 in dot_norms),
+      // timed as one group when profiling
       ProfScope group(K_GMRES, st, /*count_launch=*/false);
-      count_launches(K_GMRES, 2);
-      AIM_TRY(multidot(ws.V, ws.w, j + 1, n, nrhs, ws.dots, ws.tmp, st));
-      vcombine(ws.V, ws.dots, j + 1, n, nrhs, -1.0, ws.w, ws.tmp, st);
-      AIM_TRY(multidot(ws.V, ws.w, j + 1, n, nrhs, ws.dots2, ws.tmp, st));
-      vcombine(ws.V, ws.dots2, j + 1, n, nrhs, -1.0, ws.w, ws.tmp, st);
+      count_launches(K_GMRES, 3);
+      k_to_dfc<<<nb, tpb, 0, st>>>(ws.w, (int)vsz, ws.wdf);
+      AIM_TRY(multidot_df(ws.V, ws.wdf, j + 1, n, nrhs, ws.dots, ws.dots_df, ws.tmp, st));
+      vcombine_df(ws.V, ws.dots_df, j + 1, n, nrhs, -1.0, ws.w, ws.wdf, ws.tmp, st);
+      AIM_TRY(multidot_df(ws.V, ws.wdf, j + 1, n, nrhs, ws.dots2, ws.dots2_df, ws.tmp, st));
+      vcombine_df(ws.V, ws.dots2_df, j + 1, n, nrhs, -1.0, ws.w, nullptr, ws.tmp, st);
       k_add_small<<<blocks_for((j + 1) * nrhs, tpb), tpb, 0, st>>>(ws.dots, ws.dots2, (j + 1) * nrhs);
       AIM_TRY(dot_norms(ws.w, n, nrhs, ws.nrm, ws.tmp, st));
-      k_normalize<<<nb, tpb, 0, st>>>(ws.w, ws.nrm, ws.active, n, nrhs, ws.V + (size_t)(j + 1) * vsz);
+      k_normalize<<<nb, tpb, 0, st>>>(ws.w, ws.nrm, ws.active, n, nrhs, ws.V + (size_t)(j + 1) * vsz, ws.cur);
       AIM_CUDA_TRY(cudaGetLastError());
       AIM_CUDA_TRY(cudaMemcpyAsync(slot, ws.dots, (size_t)(j + 1) * nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
       AIM_CUDA_TRY(cudaMemcpyAsync(slot + (size_t)(j + 1) * nrhs, ws.nrm, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
@@ -426,7 +534,9 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
       }
     }
     AIM_CUDA_TRY(cudaMemcpyAsync(ws.dots, yv.data(), (size_t)jdone * nrhs * sizeof(double2), cudaMemcpyHostToDevice, st));
-    vcombine(ws.V, ws.dots, jdone, n, nrhs, 1.0, x, ws.tmp, st);
+    count_launches(K_GMRES, 1);
+    k_to_dfc<<<blocks_for((long long)jdone * nrhs, tpb), tpb, 0, st>>>(ws.dots, jdone * nrhs, ws.dots_df);
+    vcombine_df(ws.V, ws.dots_df, jdone, n, nrhs, 1.0, x, nullptr, ws.tmp, st);
     AIM_CUDA_TRY(cudaGetLastError());
     if (single_cycle) break;
   }
