@@ -61,6 +61,7 @@ def parse():
                          "stream of requests with p50/p99 latency")
     ap.add_argument("--requests", type=int, default=40, help="serving: timed requests (after 10%% warm-up)")
     ap.add_argument("--policy", choices=["sjf", "fifo"], default="sjf", help="serving: admission order")
+    ap.add_argument("--nrhs", type=int, default=64, help="batching: right-hand sides per solve (angles 2 pi r/nrhs)")
     return ap.parse_args()
 
 
@@ -408,15 +409,15 @@ def reference_arm(args):
 # batching and serving workloads (separate JSON lines; the default line is "single")
 # --------------------------------------------------------------------------------------
 def batching_arm(args):
-    """64 plane waves (angles 2 pi r/64) on one contour of perimeter 400 wl (N = 4000, 1024^2 grid),
-    all right-hand sides in every grid launch, launch schedule from the autotuner. One step = setup
-    + autotune + excitation + the batched filtered Calderon solve to 1e-5."""
+    """nrhs plane waves (default 64, angles 2 pi r/nrhs) on one contour of perimeter 400 wl
+    (N = 4000, 1024^2 grid), all right-hand sides in every grid launch, launch schedule from the
+    autotuner. One step = setup + autotune + excitation + the batched filtered Calderon solve to 1e-5."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_2606_10784_gb300 import aim
     prec = {"fp64": aim.FP64, "mixed": aim.MIXED, "native": aim.FP64_NATIVE}[args.precision]
-    wl = synth.batching_scale(args.seed, nrhs=64)
+    wl = synth.batching_scale(args.seed, nrhs=args.nrhs)
     R = len(wl.angles)
     rhs = torch.empty((R, wl.n), dtype=torch.complex128, device="cuda")
     x = torch.zeros_like(rhs)
@@ -451,8 +452,8 @@ def batching_arm(args):
             "value": args.steps * R / el, "unit": "rhs-solves/s", "n_gpus": 1, "steps": args.steps,
             "warmup": "%d x (setup + autotune + one batched product)" % max(1, args.warmup), "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
             "dtype": args.precision, "data": "synthetic",
-            "config": {"workload": "perimeter 400 wl, N=%d, grid %d^2 (P=%d), 64 plane waves, alpha=2k, GMRES(%d)"
-                                   % (wl.n, wl.m, wl.fft_P, RESTART), "schedule": last["schedule"]},
+            "config": {"workload": "perimeter 400 wl, N=%d, grid %d^2 (P=%d), %d plane waves, alpha=2k, GMRES(%d)"
+                                   % (wl.n, wl.m, wl.fft_P, R, RESTART), "schedule": last["schedule"]},
             "solve": {"status": last["status"], "iters_min": min(its), "iters_max": max(its),
                       "converged": sum(i["converged"] for i in last["info"])},
             "gpu_launches": aim.launch_count() - l0,
