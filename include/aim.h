@@ -196,7 +196,7 @@ aim_status aim_get_schedule(const aim_ctx* ctx, int precision, aim_schedule* sch
 
 /* Autotuner (no counterpart in the paper; a launch-schedule choice). Times the filtered
  * product (S^alpha) for nrhs vectors under each feasible schedule - 16 or 8 elements and one
- * or two transforms per thread, 128 or 256 row-pass threads, 1 to 8 columns per column-pass
+ * or two transforms per thread, 128, 256 or 1024 row-pass threads, 1 to 8 columns per column-pass
  * CTA - and
  * keeps the fastest for this context and precision. Synchronises `stream`. *chosen (host,
  * may be NULL) receives the winner. */

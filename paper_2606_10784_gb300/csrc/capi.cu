@@ -381,13 +381,13 @@ aim_status aim_autotune(aim_ctx* ctx, int nrhs, int precision, void* stream, aim
   Schedule best = saved;
   float best_ms = 1e30f;
   const int tpts[2] = {1, 2};
-  const int rows[2] = {128, 256};
+  const int rows[3] = {128, 256, 1024};
   const int cols[5] = {0, 1, 2, 4, 8};
   const int elems[2] = {16, 8};
   aim_status s = AIM_OK;
   for (int e = 0; e < 2 && s == AIM_OK; ++e)
   for (int a = 0; a < 2 && s == AIM_OK; ++a)
-    for (int b = 0; b < 2 && s == AIM_OK; ++b)
+    for (int b = 0; b < 3 && s == AIM_OK; ++b)
       for (int cc = 0; cc < 5 && s == AIM_OK; ++cc) {
         const Schedule cand{tpts[a], rows[b], cols[cc], elems[e]};
         if (!schedule_feasible(precision, ctx->logH, ctx->logP, cand)) continue;

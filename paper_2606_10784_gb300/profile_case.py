@@ -61,7 +61,7 @@ def main(argv=None):
     if args.sweep:
         for e in (16, 8):
             for t in (1, 2):
-                for r in (128, 256):
+                for r in (128, 256, 1024):
                     for c in (0, 1, 2, 4, 8):
                         try:
                             ctx.set_schedule(prec, t, r, c, e)
