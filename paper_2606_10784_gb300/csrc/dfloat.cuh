@@ -2,9 +2,9 @@
 //
 // GB300's FP64 rate is about 1/58 of its FP32 rate, so the FP64-accurate grid product runs its
 // FFTs in "double-float" arithmetic: every real value is an unevaluated sum hi + lo of two
-// floats with |lo| <= ulp(hi)/2 (T. J. Dekker, "A floating-point technique for extending the
-// available precision", 1971). Sums use Knuth's error-free TwoSum, products the FMA-based
-// exact product a*b = p + fma(a, b, -p). The relative error of one operation is about 2^-48
+// floats (T. J. Dekker, "A floating-point technique for extending the available precision",
+// 1971); inputs are split with |lo| <= ulp(hi)/2, results are left unnormalised (see df_add). Sums use Knuth's error-free TwoSum, products the FMA-based
+// exact product a*b = p + fma(a, b, -p). The relative error of one operation is about 2^-47
 // (sums are accurate relative to |a|+|b|, which is what the normwise error bound of an FFT
 // needs). Every operation is written with explicit round-to-nearest intrinsics so that the
 // compiler cannot contract or reassociate the error-free transformations.
@@ -24,18 +24,15 @@ __device__ __forceinline__ void ef_two_sum(float a, float b, float& s, float& e)
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// requires |a| >= |b| (or a == 0)
-__device__ __forceinline__ void ef_fast_two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  e = __fsub_rn(b, __fsub_rn(s, a));
-}
-
-// (ah + al) + (bh + bl)
+// (ah + al) + (bh + bl). Results are left unnormalised: rl may exceed half an ulp of rh. Every
+// consumer (another of these operations, the hi + lo conversion to binary64, storage) is exact
+// for such pairs, and skipping the renormalising FastTwoSum saves 3 of 11 instructions. The
+// normwise error of a 2048-point convolution round trip goes from ~9e-15 to ~2e-14.
 __device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& rh, float& rl) {
   float s, e;
   ef_two_sum(ah, bh, s, e);
-  e = __fadd_rn(e, __fadd_rn(al, bl));
-  ef_fast_two_sum(s, e, rh, rl);
+  rh = s;
+  rl = __fadd_rn(e, __fadd_rn(al, bl));
 }
 
 // (ah + al)(bh + bl) - (ch + cl)(dh + dl)  (sign = -1)  or  ... + ...  (sign = +1)
@@ -55,7 +52,8 @@ __device__ __forceinline__ void df_dot2(float ah, float al, float bh, float bl, 
   err = __fmaf_rn(al, bh, err);
   err = __fmaf_rn(cs, dl, err);
   err = __fmaf_rn(cls, dh, err);
-  ef_fast_two_sum(s, err, rh, rl);
+  rh = s;   // unnormalised, as in df_add
+  rl = err;
 }
 
 __device__ __forceinline__ dfc cadd(dfc a, dfc b) {
