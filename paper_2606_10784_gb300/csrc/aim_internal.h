@@ -163,7 +163,7 @@ struct aim_ctx {
   int reserved_rhs[3] = {0, 0, 0};   // per precision (AIM_FP64, AIM_MIXED, AIM_FP64_NATIVE)
   // launch schedule per precision; defaults measured on GB300, aim_autotune re-measures
   // defaults: measured at the single-solve scale (2048^2 grid, P = 4096), feasible at every P
-  aim::Schedule sched[3] = {{1, 128, 0, 8}, {2, 128, 0, 16}, {2, 128, 0, 16}};
+  aim::Schedule sched[3] = {{2, 128, 0, 8}, {2, 128, 0, 16}, {2, 128, 0, 16}};
   // bookkeeping
   std::vector<void*> allocations;
   size_t device_bytes = 0;
