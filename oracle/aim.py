@@ -404,6 +404,15 @@ class TEOperators(_AimBase):
         y = y - self.k ** 2 * (self._apply(pr["nx"], pr["nx"], x, False, method) + self._apply(pr["ny"], pr["ny"], x, False, method))
         return y + (self.CN @ np.asarray(x).T).T
 
+    def N_alpha(self, x, method="fft"):
+        """N (Maue form) with the numerically filtered kernel c^alpha of Eq. 10 in all three
+        projections and no near-field correction: the filter applied to the hypersingular operator
+        as Eq. 10 applies it to S."""
+        pr = self.proj
+        y = self._apply(pr["d"], pr["d"], x, True, method)
+        return y - self.k ** 2 * (self._apply(pr["nx"], pr["nx"], x, True, method) +
+                                  self._apply(pr["ny"], pr["ny"], x, True, method))
+
     def gram_solve(self, x):
         from scipy.sparse.linalg import splu
         if not hasattr(self, "_Glu"):
@@ -416,6 +425,10 @@ class TEOperators(_AimBase):
         z = self.gram_solve(self.N(x, method))
         w = self.S_alpha(z, method) if filtered else self.S(z, method)
         return self.gram_solve(w)
+
+    def calderon_both(self, x, method="fft"):
+        """G^-1 S^alpha G^-1 N^alpha x: Eq. 3 with both operators filtered."""
+        return self.gram_solve(self.S_alpha(self.gram_solve(self.N_alpha(x, method)), method))
 
 
 class TMOperators(_AimBase):

@@ -113,6 +113,18 @@ def tm_cylinder_current(phi: np.ndarray, ka: float, a: float, theta: float = 0.0
     return (c[None, :] * np.exp(1j * np.outer(phi, n))).sum(axis=1)
 
 
+def circle_mu_filtered(n: int, k: float, a: float, alpha: float) -> complex:
+    """Eigenvalue of N (Maue form) built on the analytically filtered kernel g^alpha (Eqs. 5-6).
+
+    On the circle the Maue form pairs the tangential derivatives, (n/a)^2 times the single-layer
+    eigenvalue of the mode, with the term -k^2 (n.n') g, where n.n' = cos(phi - phi') couples
+    modes n -+ 1: mu_n = (n/a)^2 lambda_n - k^2 (lambda_{n-1} + lambda_{n+1})/2. That identity
+    holds for any radial kernel, so with lambda^alpha it gives the filtered eigenvalue.
+    """
+    lam = lambda m: circle_lambda_filtered(abs(m), k, a, alpha)
+    return (n / a) ** 2 * lam(n) - k * k * (lam(n - 1) + lam(n + 1)) / 2.0
+
+
 def te_cylinder_current(phi: np.ndarray, ka: float, a: float, theta: float = 0.0,
                         nmax: int | None = None) -> np.ndarray:
     """Tangential current j_t on a PEC circle solving (eta/(j k)) N j_t = E_t (Eq. 1), H^i_z = exp(-j k khat.r).

@@ -295,6 +295,30 @@ def test_numerical_filter_converges_to_analytic_filter(circle_filtered, mode):
     assert errs[2] < 2e-2
 
 
+@pytest.mark.parametrize("mode", [0, 1, 3, 6, 10])
+def test_maue_modal_identity_reproduces_mu_n(mode):
+    # the identity behind circle_mu_filtered, checked on the unfiltered closed forms (Graf)
+    lam = lambda m: special.circle_lambda(abs(m), K, 1.0)
+    mu_id = mode ** 2 * lam(mode) - K * K * (lam(mode - 1) + lam(mode + 1)) / 2
+    mu = special.circle_mu(mode, K, 1.0)
+    assert abs(mu_id - mu) <= 1e-12 * abs(mu)
+
+
+@pytest.mark.parametrize("mode", [0, 5, 10])
+def test_numerical_filter_of_N_converges_to_analytic_filter(circle_filtered, mode):
+    # the filtered hypersingular operator: its numerical filter approaches the closed form built
+    # from Eq. 6's filtered single-layer eigenvalues, at the same rate as the S^alpha pin
+    # (errors are taken against the size of the two Maue terms, the scale of a difference that
+    # nearly cancels around n ~ ka: mu^alpha_5 is a tenth of either term at ka = 2 pi)
+    N, G, ops = circle_filtered
+    exact = special.circle_mu_filtered(mode, K, 1.0, 8 * K)
+    lam = lambda m: special.circle_lambda_filtered(abs(m), K, 1.0, 8 * K)
+    scale = mode ** 2 * abs(lam(mode)) + K * K * (abs(lam(mode - 1)) + abs(lam(mode + 1))) / 2
+    errs = [abs(_modal_op(ops[m].N_alpha, G, mode, N) - exact) / scale for m in (64, 128, 256)]
+    assert errs[1] < 0.45 * errs[0] and errs[2] < 0.45 * errs[1]
+    assert errs[2] < 1e-2
+
+
 def test_numerical_filter_truncates_beyond_alpha_a(circle_filtered):
     # Fig. 2's statement: the filtered spectrum decays exponentially after the filtering point n ~ alpha a
     N, G, ops = circle_filtered
