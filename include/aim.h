@@ -72,7 +72,10 @@ typedef enum {
   AIM_OP_CALDERON_ALPHA = 4,  /* TE only: G^-1 S^alpha G^-1 N (Eq. 3 with Eq. 10) */
   AIM_OP_GRAM_INV = 5,        /* TE only: G^-1 (G of Eq. 3) */
   AIM_OP_EFIE = 6,            /* system matrix of the EFIE: TM j k eta S ; TE N (Eq. 1 scaled by jk/eta) */
-  AIM_OP_EFIE_ALPHA = 7       /* TM only: j k eta S^alpha */
+  AIM_OP_EFIE_ALPHA = 7,      /* TM only: j k eta S^alpha */
+  AIM_OP_N_ALPHA = 8,         /* TE only: N with the filtered kernel of Eq. 10 in all three
+                                 projections, no near-field correction */
+  AIM_OP_CALDERON_ALPHA2 = 9  /* TE only: G^-1 S^alpha G^-1 N^alpha (Eq. 3, both operators filtered) */
 } aim_op;
 
 /* Grid arithmetic of a product (vectors are complex128 in every mode):
@@ -251,7 +254,7 @@ aim_status aim_grid_product_noalloc(aim_ctx* ctx, int filtered, int nrhs, const 
 
 /* Solves A x = b for nrhs right-hand sides by restarted GMRES with FP64 Arnoldi
  * (classical Gram-Schmidt, applied twice). `system` is AIM_OP_EFIE, AIM_OP_EFIE_ALPHA,
- * AIM_OP_CALDERON or AIM_OP_CALDERON_ALPHA. For the Calderon systems `rhs` is the EFIE
+ * AIM_OP_CALDERON, AIM_OP_CALDERON_ALPHA or AIM_OP_CALDERON_ALPHA2. For the Calderon systems `rhs` is the EFIE
  * excitation E and the solver forms G^-1 S G^-1 E itself (Eq. 3). In AIM_MIXED precision
  * the inner GMRES uses the FP32 grid product and the outer loop refines with FP64
  * residuals until opts->tol. x is both the initial guess (if x0_given != 0) and the

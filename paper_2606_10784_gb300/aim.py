@@ -19,11 +19,13 @@ LIB_PATH = os.path.join(HERE, "libaimgb300.so")
 # enums (mirror include/aim.h)
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, ENUMERIC, ETIMEOUT, ESTATE = range(8)
 TM, TE = 0, 1
-OP_S, OP_S_ALPHA, OP_N, OP_CALDERON, OP_CALDERON_ALPHA, OP_GRAM_INV, OP_EFIE, OP_EFIE_ALPHA = range(8)
+(OP_S, OP_S_ALPHA, OP_N, OP_CALDERON, OP_CALDERON_ALPHA, OP_GRAM_INV, OP_EFIE, OP_EFIE_ALPHA, OP_N_ALPHA,
+ OP_CALDERON_ALPHA2) = range(10)
 FP64, MIXED, FP64_NATIVE = 0, 1, 2
 
 OPS = {"S": OP_S, "S_alpha": OP_S_ALPHA, "N": OP_N, "calderon": OP_CALDERON,
-       "calderon_alpha": OP_CALDERON_ALPHA, "gram_inv": OP_GRAM_INV, "efie": OP_EFIE, "efie_alpha": OP_EFIE_ALPHA}
+       "calderon_alpha": OP_CALDERON_ALPHA, "gram_inv": OP_GRAM_INV, "efie": OP_EFIE, "efie_alpha": OP_EFIE_ALPHA,
+       "N_alpha": OP_N_ALPHA, "calderon_alpha2": OP_CALDERON_ALPHA2}
 
 
 class Geometry(ctypes.Structure):

@@ -114,6 +114,15 @@ static PassSpec make_spec(const aim_ctx* ctx, aim_op op) {
       s.near = &ctx->near;
       s.near_which = 1;
       break;
+    case AIM_OP_N_ALPHA:
+      s.nproj = 3;
+      s.proj[0] = 1; s.proj[1] = 2; s.proj[2] = 3;
+      s.coef[0] = double2{1.0, 0.0};
+      s.coef[1] = double2{-k2, 0.0};
+      s.coef[2] = double2{-k2, 0.0};
+      s.filtered = true;
+      s.near = nullptr;
+      break;
     case AIM_OP_S_ALPHA:
     case AIM_OP_EFIE_ALPHA:
       s.nproj = 1;
@@ -151,6 +160,7 @@ aim_status apply_op(aim_ctx* ctx, aim_op op, int nrhs, const double2* x, double2
     case AIM_OP_S_ALPHA:
       return pass(ctx, op, nrhs, x, y, precision, st);
     case AIM_OP_N:
+    case AIM_OP_N_ALPHA:
       if (!te) return fail(AIM_ESTATE, "N is a TE operator");
       return pass(ctx, op, nrhs, x, y, precision, st);
     case AIM_OP_EFIE:
@@ -162,12 +172,14 @@ aim_status apply_op(aim_ctx* ctx, aim_op op, int nrhs, const double2* x, double2
       if (!te) return fail(AIM_ESTATE, "G is a TE operator");
       return gram_inv_apply(ctx, nrhs, x, y, st);
     case AIM_OP_CALDERON:
-    case AIM_OP_CALDERON_ALPHA: {
+    case AIM_OP_CALDERON_ALPHA:
+    case AIM_OP_CALDERON_ALPHA2: {
       if (!te) return fail(AIM_ESTATE, "the Calderon product is a TE operator");
-      // y = G^-1 S G^-1 N x  (Eq. 3), S^alpha of Eq. 10 for the filtered variant
+      // y = G^-1 S G^-1 N x  (Eq. 3), S^alpha of Eq. 10 for the filtered variants, N^alpha too
+      // for the doubly filtered one
       double2* t1 = ctx->vec_ws;
       double2* t2 = ctx->vec_ws + (size_t)nrhs * ctx->n;
-      AIM_TRY(pass(ctx, AIM_OP_N, nrhs, x, t1, precision, st));
+      AIM_TRY(pass(ctx, op == AIM_OP_CALDERON_ALPHA2 ? AIM_OP_N_ALPHA : AIM_OP_N, nrhs, x, t1, precision, st));
       AIM_TRY(gram_inv_apply(ctx, nrhs, t1, t2, st));
       AIM_TRY(pass(ctx, op == AIM_OP_CALDERON ? AIM_OP_S : AIM_OP_S_ALPHA, nrhs, t2, t1, precision, st));
       return gram_inv_apply(ctx, nrhs, t1, y, st);
@@ -491,9 +503,11 @@ aim_status aim_solve(aim_ctx* ctx, aim_op system, int nrhs, const void* rhs, voi
     return fail(AIM_EINVAL, "bad solver options");
   if (opts->precision < AIM_FP64 || opts->precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "bad precision");
   const bool te = ctx->form == AIM_TE_P1_GALERKIN;
-  if (system != AIM_OP_EFIE && system != AIM_OP_EFIE_ALPHA && system != AIM_OP_CALDERON && system != AIM_OP_CALDERON_ALPHA)
-    return fail(AIM_EINVAL, "system must be EFIE, EFIE_ALPHA, CALDERON or CALDERON_ALPHA");
-  if (!te && (system == AIM_OP_CALDERON || system == AIM_OP_CALDERON_ALPHA))
+  const bool calderon =
+      system == AIM_OP_CALDERON || system == AIM_OP_CALDERON_ALPHA || system == AIM_OP_CALDERON_ALPHA2;
+  if (system != AIM_OP_EFIE && system != AIM_OP_EFIE_ALPHA && !calderon)
+    return fail(AIM_EINVAL, "system must be EFIE, EFIE_ALPHA, CALDERON, CALDERON_ALPHA or CALDERON_ALPHA2");
+  if (!te && calderon)
     return fail(AIM_ESTATE, "Calderon systems need a TE context");
   if (te && system == AIM_OP_EFIE_ALPHA) return fail(AIM_ESTATE, "filtered EFIE system is TM only");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -512,8 +526,8 @@ aim_status aim_solve(aim_ctx* ctx, aim_op system, int nrhs, const void* rhs, voi
   } else {
     AIM_CUDA_TRY(cudaMemsetAsync(xd, 0, bytes, st));
   }
-  if (system == AIM_OP_CALDERON || system == AIM_OP_CALDERON_ALPHA) {
-    // b <- G^-1 S G^-1 E, with S^alpha for the filtered system (Eq. 3)
+  if (calderon) {
+    // b <- G^-1 S G^-1 E, with S^alpha for the filtered systems (Eq. 3)
     double2* t1 = ctx->vec_ws;
     double2* t2 = ctx->vec_ws + (size_t)nrhs * ctx->n;
     AIM_TRY(gram_inv_apply(ctx, nrhs, b, t1, st));

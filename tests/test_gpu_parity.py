@@ -102,14 +102,15 @@ def te_pair(request, aimlib):
     ctx.close()
 
 
-@pytest.mark.parametrize("op", ["S", "S_alpha", "N", "gram_inv", "calderon", "calderon_alpha", "efie"])
+@pytest.mark.parametrize("op", ["S", "S_alpha", "N", "N_alpha", "gram_inv", "calderon", "calderon_alpha",
+                                "calderon_alpha2", "efie"])
 def test_te_operator_matches_oracle(te_pair, op):
     nodes, ctx, ref = te_pair
     n = len(nodes)
     x = synth.random_coeffs(n, 3, seed=7)
-    f = {"S": ref.S, "S_alpha": ref.S_alpha, "N": ref.N, "gram_inv": ref.gram_solve,
+    f = {"S": ref.S, "S_alpha": ref.S_alpha, "N": ref.N, "N_alpha": ref.N_alpha, "gram_inv": ref.gram_solve,
          "calderon": lambda v: ref.calderon(v, filtered=False), "calderon_alpha": lambda v: ref.calderon(v, True),
-         "efie": ref.N}[op]
+         "calderon_alpha2": ref.calderon_both, "efie": ref.N}[op]
     want = np.stack([f(v) for v in x])
     for prec in (0, 2):       # FP64 (double-float grid arithmetic) and native FP64
         got = run_matvec(ctx, op, x, precision=prec)
@@ -255,6 +256,20 @@ def test_te_filtered_calderon_solve_residual_under_oracle(te_pair, precision):
     assert info[0]["converged"] == 1
     xs = x.cpu().numpy()[0]
     assert np.linalg.norm(b - ref.calderon(xs, True)) / np.linalg.norm(b) < 100 * tol
+
+
+def test_te_doubly_filtered_calderon_solve_residual_under_oracle(te_pair):
+    # G^-1 S^alpha G^-1 N^alpha x = G^-1 S^alpha G^-1 E: both operators filtered; nearly singular
+    # beyond alpha a like the singly filtered system, so its residual is checked under the oracle
+    nodes, ctx, ref = te_pair
+    E = dense.te_rhs(nodes, K, 0.3)
+    b = ref.gram_solve(ref.S_alpha(ref.gram_solve(E)))
+    rhs = dev(E[None])
+    x = torch.zeros_like(rhs)
+    info = ctx.solve("calderon_alpha2", rhs, x, tol=1e-10, restart=1000, max_iter=4000, precision=0)
+    assert info[0]["converged"] == 1
+    xs = x.cpu().numpy()[0]
+    assert np.linalg.norm(b - ref.calderon_both(xs)) / np.linalg.norm(b) < 1e-8
 
 
 @pytest.mark.parametrize("precision", [0, 1, 2])
