@@ -189,6 +189,12 @@ def col_conv_algorithmic(wl, info, precision, channels):
 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz = 80.5
 
+# DRAM traffic of k_col_conv per launch (dram__bytes_read.sum + dram__bytes_write.sum), the mean of
+# the two launches of one filtered Calderon product (N: 3 channels, S^alpha: 1 channel), from one
+# ncu capture of the default schedule at the single-solve size; the profiles directory gives the
+# capture and its command. None where no capture matches the current kernel and schedule.
+COL_CONV_TRAFFIC = {"fp64": 575781248, "mixed": 222040192, "native": None}
+
 
 def aggregate(elapsed: float, steps: int, world: int, device=None):
     """Max-over-ranks elapsed time and the whole-job rate (all ranks' steps / that time).
@@ -295,6 +301,7 @@ def gb300_arm(args):
     if rank != 0:
         return None
     # roofline of the dominant kernel (largest total time in the timed region)
+    traffic = COL_CONV_TRAFFIC.get(args.precision)
     peaks, src = load_peaks()
     top = max(prof.items(), key=lambda kv: kv[1][1])
     name, (nl, tms) = top
@@ -313,7 +320,7 @@ def gb300_arm(args):
             peak = FP32_PEAK_TFLOPS if args.precision == "fp64" else FP64_PEAK_TFLOPS
             ach = per_launch_flops / avg_s / 1e12
             roof = {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": None,
+                    "frac": ach / peak, "traffic": traffic if name.startswith("col_conv") else None,
                     "peak_source": ("FP32 pipe nominal: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived; "
                                     "MEASURED_PEAKS has no FP32 figure); flops counted in double-float arithmetic"
                                     if args.precision == "fp64" else
@@ -325,12 +332,12 @@ def gb300_arm(args):
         else:
             ach = per_launch_bytes / avg_s / 1e9
             roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": src,
+                    "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "peak_source": src,
                     "launches": nl, "avg_launch_ms": avg_s * 1e3}
     kernels = {k: {"launches": v[0], "total_ms": round(v[1], 3)} for k, v in prof.items()}
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": max(3, args.warmup), "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "df64 (complex fp32-pair double-float grid; c128 vectors, f64 Arnoldi)",
+           "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "df64 (complex fp32-pair double-float grid and Gram-Schmidt products; c128 vectors)",
                                                    "mixed": "c64 grid + f64 refinement",
                                                    "native": "c128"}[args.precision],
            "data": "synthetic (seeded random smooth contour family)",
