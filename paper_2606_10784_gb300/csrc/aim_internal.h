@@ -143,6 +143,8 @@ struct aim_ctx {
   float2* specAf = nullptr;
   float4* specUdf = nullptr;   // double-float copies (re hi, re lo, im hi, im lo)
   float4* specAdf = nullptr;
+  // per column q' = 0..H of the filtered spectrum: 0 when the mask zeroes the whole column
+  int* specA_live = nullptr;
   double2* tw = nullptr;    // e^{-2 pi i t / P}, t < P
   float2* twf = nullptr;
   float4* twdf = nullptr;

@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_fwd(Row
 struct ColArgs {
   void* inter;
   const void* spec;
+  const int* live;     // filtered spectrum: per column q' <= P/2, 0 where the mask zeroes it; else null
   const void* tw;
   int logH, logP, row_lo, nrows;
   int log_cols;        // log2 of the columns of one channel per CTA
@@ -183,6 +184,26 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_col_conv(Co
   const int qcol = (blockIdx.x << a.log_cols) + colc;   // column of the grid
   const int w = qcol & (W - 1), tile = qcol / W;
   const int c = blockIdx.y;
+  if (a.live != nullptr) {
+    // the filtered spectrum (Eq. 10) vanishes on columns beyond the mask radius: when it does on
+    // every column of this CTA their product is zero, so write zeros and skip the transforms
+    // (the same decision in every thread: the early return is uniform)
+    bool any = false;
+    for (int cc = 0; cc < (1 << a.log_cols); ++cc) {
+      const int q = (blockIdx.x << a.log_cols) + cc;
+      any = any || a.live[min(q, P - q)] != 0;
+    }
+    if (!any) {
+      T2* base = static_cast<T2*>(a.inter) + (size_t)c * P * a.nrows;
+      const int total = (1 << a.log_cols) * a.nrows;
+      for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int cc = e / a.nrows, row = e - cc * a.nrows;
+        const int q = (blockIdx.x << a.log_cols) + cc;
+        base[((size_t)(q / W) * a.nrows + row) * W + (q & (W - 1))] = czero<T2>();
+      }
+      return;
+    }
+  }
   int fb[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) fb[f] = (2 * colc + (TPT == 1 ? half : f)) * HS;
@@ -553,6 +574,7 @@ static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdAr
   ColArgs ca;
   ca.inter = ctx->inter;
   ca.spec = spec;
+  ca.live = filtered ? ctx->specA_live : nullptr;
   ca.tw = tw;
   ca.logH = ctx->logH;
   ca.logP = ctx->logP;

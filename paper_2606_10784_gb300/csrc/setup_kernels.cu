@@ -116,9 +116,12 @@ __device__ __forceinline__ float4 split_df(double2 v) {
   return float4{xh, __double2float_rn(v.x - (double)xh), yh, __double2float_rn(v.y - (double)yh)};
 }
 
+// live[q'] = 0 when the mask zeroes column q' entirely. kappa(p, q') >= kappa(0, q') holds in
+// floating point as well (sqrt is exact on the perfect square q'^2 and monotone, and both are
+// scaled by the same factor), so the column has a kept entry exactly when its p = 0 entry is kept.
 __global__ void k_pack_spectrum(const double2* C, int H, int P, double eps, double alpha, int filter,
                                 double2* specU, double2* specA, float2* specUf, float2* specAf, float4* specUdf,
-                                float4* specAdf) {
+                                float4* specAdf, int* live) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long total = (long long)(H + 1) * (H + 1);
   if (t >= total) return;
@@ -135,6 +138,7 @@ __global__ void k_pack_spectrum(const double2* C, int H, int P, double eps, doub
   specAf[t] = float2{(float)va.x, (float)va.y};
   specUdf[t] = split_df(v);
   specAdf[t] = split_df(va);
+  if (off == 0) live[qq] = keep ? 1 : 0;   // p = 0
 }
 
 // ------------------------------------------------------------------------------------
@@ -633,13 +637,14 @@ aim_status device_spectra_and_near(aim_ctx* ctx, const HostSetup& hs, cudaStream
   AIM_TRY(dev_alloc_t(ctx, &ctx->specAf, nq));
   AIM_TRY(dev_alloc_t(ctx, &ctx->specUdf, nq));
   AIM_TRY(dev_alloc_t(ctx, &ctx->specAdf, nq));
+  AIM_TRY(dev_alloc_t(ctx, &ctx->specA_live, (size_t)H + 1));
   {
     const int tpb = 256;
     ProfScope ps(K_SETUP_PACK, st);
     k_pack_spectrum<<<(unsigned)((nq + tpb - 1) / tpb), tpb, 0, st>>>(samp, H, P, ctx->eps, ctx->alpha,
                                                                       ctx->filter_enabled, ctx->specU, ctx->specA,
                                                                       ctx->specUf, ctx->specAf, ctx->specUdf,
-                                                                      ctx->specAdf);
+                                                                      ctx->specAdf, ctx->specA_live);
     AIM_CUDA_TRY(cudaGetLastError());
   }
   // temporaries are freed when `tmp` goes out of scope: wait for the kernels first
