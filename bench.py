@@ -167,13 +167,15 @@ def fft_flops(logh: int, kind: str) -> float:
     return total
 
 
-def col_conv_algorithmic(wl, info, precision, channels):
+def col_conv_algorithmic(wl, info, precision, channels, filtered=False):
     """Algorithmic work of one column-pass launch (the dominant kernel).
 
     Bytes: each channel's m_rows x P intermediate read once and written once, plus the stored
-    (P/2+1)^2 spectrum read once per channel. Flops: per column and channel four half-length
+    (P/2+1)^2 spectrum read once per launch (all channels use the same spectrum). Flops: per column and channel four half-length
     transforms (fft_flops), the w^n twiddle of the odd half, the spectral product of P points
-    and the recombination y = A + conj(w^n) B at every one of the H rows.
+    and the recombination y = A + conj(w^n) B at every one of the H rows. For the filtered
+    spectrum only the columns that the mask keeps count (2 pi min(q, P - q) / (P eps) <= alpha):
+    the others need no transform, only a zero written per row.
     """
     P = wl.fft_P
     H = P // 2
@@ -181,9 +183,13 @@ def col_conv_algorithmic(wl, info, precision, channels):
     kind = "df" if precision == "fp64" else "plain"
     add, mul = CPLX_COST[kind]
     b = 8 if precision == "mixed" else 16
-    bytes_ = channels * (2 * rows * P * b + (H + 1) ** 2 * b)
+    live_half = H + 1
+    if filtered:
+        live_half = sum(1 for q in range(H + 1) if 2.0 * math.pi * q / (P * info["eps"]) <= info["alpha"])
+    live = sum(1 for q in range(P) if min(q, P - q) < live_half)
+    bytes_ = channels * (2 * rows * live * b + rows * (P - live) * b) + live_half * (H + 1) * b
     per_col = 4 * fft_flops(int(math.log2(H)), kind) + H * mul + P * mul + H * (mul + add)
-    flops = channels * P * per_col
+    flops = channels * live * per_col
     return bytes_, flops
 
 
@@ -193,7 +199,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x 
 # the two launches of one filtered Calderon product (N: 3 channels, S^alpha: 1 channel), from one
 # ncu capture of the default schedule at the single-solve size; the profiles directory gives the
 # capture and its command. None where no capture matches the current kernel and schedule.
-COL_CONV_TRAFFIC = {"fp64": None, "mixed": None, "native": None}
+COL_CONV_TRAFFIC = {"fp64": 532714496, "mixed": 202739328, "native": None}
 
 
 def aggregate(elapsed: float, steps: int, world: int, device=None):
@@ -312,7 +318,7 @@ def gb300_arm(args):
         # the Calderon product runs 3 channels (N) and 1 channel (S^alpha) per application
         n_n = nl // 2
         b3, f3 = col_conv_algorithmic(wl, info, args.precision, 3)
-        b1, f1 = col_conv_algorithmic(wl, info, args.precision, 1)
+        b1, f1 = col_conv_algorithmic(wl, info, args.precision, 1, filtered=True)
         per_launch_bytes = (b3 + b1) / 2
         per_launch_flops = (f3 + f1) / 2
         if args.precision in ("fp64", "native"):
