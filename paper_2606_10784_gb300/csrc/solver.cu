@@ -137,6 +137,8 @@ __global__ void k_multidot_partial_df(const dfc* __restrict__ V, const dfc* __re
   const dfc* v = V + ((size_t)j * nrhs + r) * n;
   const dfc* x = w + (size_t)r * n;
   float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+  // independent loads, dependent sums: unrolled so that the loads are issued ahead
+#pragma unroll 4
   for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const dfc a = v[i], b = x[i];
     float ph, pl;
@@ -192,6 +194,8 @@ __global__ void k_vcombine_partial_df(const dfc* __restrict__ V, const dfc* __re
   if (i >= n) return;
   const int j0 = chunk * kCgsChunk, j1 = min(J, j0 + kCgsChunk);
   float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+  // independent loads, dependent sums: unrolled so that the loads are issued ahead
+#pragma unroll 8
   for (int j = j0; j < j1; ++j) {
     const dfc v = V[((size_t)j * nrhs + r) * n + i];
     const dfc h = c[(size_t)j * nrhs + r];
