@@ -184,43 +184,24 @@ __global__ void k_multidot_finish_df(const double2* __restrict__ part, int nz, i
   out_df[t] = to_dfc(double2{re, im});
 }
 
-// Stage 1 of the basis update: part[chunk][r][i] = sum over the chunk of V[j][r][i] c[j*nrhs + r].
-// A CTA covers 32 elements x the chunk's kCgsChunk vectors: warp g sums the vectors
-// j0 + g, j0 + g + 8, ... in double-float, and the 8 warp sums are added in warp order (FP64)
-// through shared memory, so the result is deterministic. (A thread per element walking all 32
-// vectors left few CTAs in flight at small basis sizes, each a long chain of loads.)
-constexpr int kCgsGroups = 8;
-__global__ void __launch_bounds__(32 * kCgsGroups) k_vcombine_partial_df(const dfc* __restrict__ V,
-                                                                         const dfc* __restrict__ c, int J, int n,
-                                                                         int nrhs, double2* __restrict__ part) {
-  const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
-  const int i = blockIdx.x * 32 + lane;
+// Stage 1 of the basis update: part[chunk][r][i] = sum over the chunk of V[j][r][i] c[j*nrhs + r]
+__global__ void k_vcombine_partial_df(const dfc* __restrict__ V, const dfc* __restrict__ c, int J, int n, int nrhs,
+                                      double2* __restrict__ part) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int chunk = blockIdx.y, r = blockIdx.z;
+  if (i >= n) return;
   const int j0 = chunk * kCgsChunk, j1 = min(J, j0 + kCgsChunk);
   float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-  if (i < n) {
-    for (int j = j0 + g; j < j1; j += kCgsGroups) {
-      const dfc v = V[((size_t)j * nrhs + r) * n + i];
-      const dfc h = c[(size_t)j * nrhs + r];
-      float ph, pl;
-      df_dot2<-1>(v.xh, v.xl, h.xh, h.xl, v.yh, v.yl, h.yh, h.yl, ph, pl);   // vx hx - vy hy
-      df_add(rh, rl, ph, pl, rh, rl);
-      df_dot2<+1>(v.xh, v.xl, h.yh, h.yl, v.yh, v.yl, h.xh, h.xl, ph, pl);   // vx hy + vy hx
-      df_add(ih, il, ph, pl, ih, il);
-    }
+  for (int j = j0; j < j1; ++j) {
+    const dfc v = V[((size_t)j * nrhs + r) * n + i];
+    const dfc h = c[(size_t)j * nrhs + r];
+    float ph, pl;
+    df_dot2<-1>(v.xh, v.xl, h.xh, h.xl, v.yh, v.yl, h.yh, h.yl, ph, pl);   // vx hx - vy hy
+    df_add(rh, rl, ph, pl, rh, rl);
+    df_dot2<+1>(v.xh, v.xl, h.yh, h.yl, v.yh, v.yl, h.xh, h.xl, ph, pl);   // vx hy + vy hx
+    df_add(ih, il, ph, pl, ih, il);
   }
-  __shared__ double2 sg[kCgsGroups][32];
-  sg[g][lane] = to_d2(rh, rl, ih, il);
-  __syncthreads();
-  if (g == 0 && i < n) {
-    double re = 0.0, im = 0.0;
-#pragma unroll
-    for (int q = 0; q < kCgsGroups; ++q) {
-      re += sg[q][lane].x;
-      im += sg[q][lane].y;
-    }
-    part[((size_t)chunk * nrhs + r) * n + i] = double2{re, im};
-  }
+  part[((size_t)chunk * nrhs + r) * n + i] = to_d2(rh, rl, ih, il);
 }
 
 // Stage 2: out += sign * sum of the chunk partials (FP64, in chunk order); out_df (may be null)
@@ -334,7 +315,7 @@ static void vcombine_df(const dfc* V, const dfc* c, int J, int n, int nrhs, doub
                         double2* part, cudaStream_t st) {
   const int nch = (J + kCgsChunk - 1) / kCgsChunk;
   count_launches(K_GMRES, 2);
-  k_vcombine_partial_df<<<dim3((n + 31) / 32, nch, nrhs), 32 * kCgsGroups, 0, st>>>(V, c, J, n, nrhs, part);
+  k_vcombine_partial_df<<<dim3((n + 255) / 256, nch, nrhs), 256, 0, st>>>(V, c, J, n, nrhs, part);
   k_vcombine_finish_df<<<(n * nrhs + 255) / 256, 256, 0, st>>>(part, nch, n, nrhs, sign, out, out_df);
 }
 
