@@ -43,6 +43,8 @@ enum KernelId {
   K_RHS, K_GMRES, K_COUNT
 };
 void count_launches(int id, int n);   // counted, not timed
+void thread_launch_counts(long long* out);   // this host thread's counts, K_COUNT entries
+bool profiling_active();
 struct ProfScope {
   // count_launch = false: a timing-only scope around a group of launches counted elsewhere
   ProfScope(int id, cudaStream_t st, bool count_launch = true);

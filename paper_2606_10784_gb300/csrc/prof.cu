@@ -35,7 +35,17 @@ std::vector<Slot> g_pool;
 size_t g_used = 0;
 }  // namespace
 
-void count_launches(int id, int n) { g_launches[id].fetch_add(n, std::memory_order_relaxed); }
+// the same counts per host thread (a capture reads its own launches without other threads')
+thread_local long long tl_launches[K_COUNT];
+
+void count_launches(int id, int n) {
+  g_launches[id].fetch_add(n, std::memory_order_relaxed);
+  tl_launches[id] += n;
+}
+
+void thread_launch_counts(long long* out) {
+  for (int i = 0; i < K_COUNT; ++i) out[i] = tl_launches[i];
+}
 
 bool profiling_active() {
   std::lock_guard<std::mutex> lk(g_mu);
@@ -43,7 +53,10 @@ bool profiling_active() {
 }
 
 ProfScope::ProfScope(int id_, cudaStream_t st_, bool count_launch) : id(id_), st(st_), slot(-1) {
-  if (count_launch) g_launches[id].fetch_add(1, std::memory_order_relaxed);
+  if (count_launch) {
+    g_launches[id].fetch_add(1, std::memory_order_relaxed);
+    tl_launches[id] += 1;
+  }
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_timing) return;
   if (g_used == g_pool.size()) {

@@ -299,6 +299,47 @@ aim_status dot_norms(const double2* vecs, int n, int nrhs, double2* out, double2
 
 }  // namespace
 
+// The operator product of an Arnoldi step always reads the current vector and writes w, so it is
+// captured once as a CUDA graph and replayed each iteration: one host call instead of ~10 kernel
+// launches, which is what limits small problems. Not while kernels are being timed (a replay
+// would not record their events); if capture fails for any reason the step launches directly.
+struct OpGraph {
+  cudaGraphExec_t exec = nullptr;
+  bool tried = false;
+  long long counts[K_COUNT] = {};   // launches one replay stands for, per kernel id
+  void capture(aim_ctx* ctx, aim_op op, int nrhs, const double2* x, double2* y, int precision, cudaStream_t st) {
+    tried = true;
+    if (profiling_active()) return;
+    long long before[K_COUNT], after[K_COUNT];
+    thread_launch_counts(before);
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return;
+    }
+    const aim_status s = apply_op(ctx, op, nrhs, x, y, precision, st);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &g);
+    thread_launch_counts(after);
+    for (int i = 0; i < K_COUNT; ++i) {
+      counts[i] = after[i] - before[i];
+      if (counts[i]) count_launches(i, (int)-counts[i]);   // a capture runs nothing
+    }
+    if (s == AIM_OK && e == cudaSuccess && g != nullptr && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess)
+      exec = nullptr;
+    if (g != nullptr) cudaGraphDestroy(g);
+    cudaGetLastError();
+  }
+  aim_status replay(cudaStream_t st) {
+    AIM_CUDA_TRY(cudaGraphLaunch(exec, st));
+    for (int i = 0; i < K_COUNT; ++i)
+      if (counts[i]) count_launches(i, (int)counts[i]);
+    return AIM_OK;
+  }
+  ~OpGraph() {
+    if (exec != nullptr) cudaGraphExecDestroy(exec);
+  }
+};
+
 // out[j*nrhs + r] = <V[j][r], w[r]> for j < J over the double-float basis (two launches)
 static aim_status multidot_df(const dfc* V, const dfc* w, int J, int n, int nrhs, double2* out, dfc* out_df,
                               double2* part, cudaStream_t st) {
@@ -408,6 +449,7 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
   std::vector<int> jconv(nrhs);
   EventPair col_ready;
   AIM_TRY(col_ready.create());
+  OpGraph op_graph;
 
   while (true) {
     // true residual r = b - A x
@@ -448,7 +490,13 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
     // useful one is discarded).
     auto arnoldi_step = [&](int j) -> aim_status {
       double2* slot = hred + (size_t)(j & 1) * (restart + 2) * nrhs;
-      AIM_TRY(apply_op(ctx, op, nrhs, ws.cur, ws.w, precision, st));   // cur = v_j
+      // w = A v_j (cur = v_j)
+      if (!op_graph.tried) op_graph.capture(ctx, op, nrhs, ws.cur, ws.w, precision, st);
+      if (op_graph.exec != nullptr) {
+        AIM_TRY(op_graph.replay(st));
+      } else {
+        AIM_TRY(apply_op(ctx, op, nrhs, ws.cur, ws.w, precision, st));
+      }
       // CGS2 (3 launches here + 2 x 2 in multidot_df + 2 x 2 in vcombine_df + 2 in dot_norms),
       // timed as one group when profiling
       ProfScope group(K_GMRES, st, /*count_launch=*/false);

@@ -258,6 +258,28 @@ def test_te_filtered_calderon_solve_residual_under_oracle(te_pair, precision):
     assert np.linalg.norm(b - ref.calderon(xs, True)) / np.linalg.norm(b) < 100 * tol
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_on_a_stream_replays_the_captured_operator_bit_for_bit(te_pair, aimlib, precision):
+    # on a non-default stream the Arnoldi step's operator product is captured once and replayed
+    # as a CUDA graph (the legacy default stream cannot be captured, so it launches directly):
+    # same kernels, same order, so the same bits, the same iterations and the same launch count
+    nodes, ctx, ref = te_pair
+    E = dense.te_rhs(nodes, K, 0.3)
+    rhs = dev(E[None])
+    x0, x1 = torch.zeros_like(rhs), torch.zeros_like(rhs)
+    l0 = aimlib.launch_count()
+    i0 = ctx.solve("calderon", rhs, x0, tol=1e-10, restart=100, precision=precision)
+    l1 = aimlib.launch_count()
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    i1 = ctx.solve("calderon", rhs, x1, tol=1e-10, restart=100, precision=precision, stream=s)
+    s.synchronize()
+    l2 = aimlib.launch_count()
+    assert i0 == i1
+    assert torch.equal(x0, x1)
+    assert l2 - l1 == l1 - l0
+
+
 def test_te_doubly_filtered_calderon_solve_residual_under_oracle(te_pair):
     # G^-1 S^alpha G^-1 N^alpha x = G^-1 S^alpha G^-1 E: both operators filtered; nearly singular
     # beyond alpha a like the singly filtered system, so its residual is checked under the oracle
