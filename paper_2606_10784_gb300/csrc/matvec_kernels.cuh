@@ -88,39 +88,16 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_fwd(Row
       const double* w = a.w[pj];
       const double2* xv = a.x + (size_t)r * a.n;
       const int a1 = a.row_ptr[iy + 1];
-      if ((per_row & 31) == 0) {
-        // a warp per active point: the lanes take the point's entries e = lane, lane + 32, ...
-        // and reduce by shuffles in a fixed order (a thread per point left the other threads of
-        // the CTA waiting at the barrier behind a chain of dependent loads)
-        const int lane = rem & 31, wp = rem >> 5, nwp = per_row >> 5;
-        for (int ap = a.row_ptr[iy] + wp; ap < a1; ap += nwp) {
-          double re = 0.0, im = 0.0;
-          const int e1 = a.sc_ptr[ap + 1];
-          for (int e = a.sc_ptr[ap] + lane; e < e1; e += 32) {
-            const double ww = w[e];
-            const double2 xx = xv[a.sc_col[e]];
-            re = fma(ww, xx.x, re);
-            im = fma(ww, xx.y, im);
-          }
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) {
-            re += __shfl_xor_sync(0xffffffffu, re, off);
-            im += __shfl_xor_sync(0xffffffffu, im, off);
-          }
-          if (lane == 0) sm[fbA + padi<LOGE>(a.act_ix[ap])] = cfrom<T2>(re, im);
+      for (int ap = a.row_ptr[iy] + rem; ap < a1; ap += per_row) {
+        double re = 0.0, im = 0.0;
+        const int e1 = a.sc_ptr[ap + 1];
+        for (int e = a.sc_ptr[ap]; e < e1; ++e) {
+          const double ww = w[e];
+          const double2 xx = xv[a.sc_col[e]];
+          re = fma(ww, xx.x, re);
+          im = fma(ww, xx.y, im);
         }
-      } else {
-        for (int ap = a.row_ptr[iy] + rem; ap < a1; ap += per_row) {
-          double re = 0.0, im = 0.0;
-          const int e1 = a.sc_ptr[ap + 1];
-          for (int e = a.sc_ptr[ap]; e < e1; ++e) {
-            const double ww = w[e];
-            const double2 xx = xv[a.sc_col[e]];
-            re = fma(ww, xx.x, re);
-            im = fma(ww, xx.y, im);
-          }
-          sm[fbA + padi<LOGE>(a.act_ix[ap])] = cfrom<T2>(re, im);
-        }
+        sm[fbA + padi<LOGE>(a.act_ix[ap])] = cfrom<T2>(re, im);
       }
     }
   }
