@@ -261,15 +261,9 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_col_conv(Co
 struct RowInvArgs {
   const void* inter;
   const void* tw;
-  void* vact;          // sparse mode output (see rhs_fast)
+  void* vact;          // sparse mode output: channel-major, n_act per channel
   double2* dense_out;  // dense mode output: m*m per channel
   int dense;
-  // sparse mode with several right-hand sides: channel c = pj * nrhs + r is stored at
-  // vact[(pj * n_act + ap) * nrhs + r] (right-hand side fastest, so a gather warp reads the
-  // values of one active point for a block of right-hand sides from adjacent bytes), and the
-  // grid runs channels along x so that the CTAs filling one such group run close in time.
-  // Otherwise (one right-hand side, rhs_fast = 0) vact[c * n_act + ap].
-  int rhs_fast, nrhs;
   int m, n_act;
   const int* row_ptr;
   const int* act_ix;
@@ -289,8 +283,8 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_inv(Row
   const int per_row = LPT * tpf;
   const int g = threadIdx.x / per_row, rem = threadIdx.x - g * per_row;
   const int half = TPT == 1 ? (rem & 1) : 0, j = TPT == 1 ? (rem >> 1) : rem;
-  const int rloc = (a.rhs_fast ? blockIdx.y : blockIdx.x) * a.rows_per_cta + g;
-  const int c = a.rhs_fast ? blockIdx.x : blockIdx.y;
+  const int rloc = blockIdx.x * a.rows_per_cta + g;
+  const int c = blockIdx.y;
   const bool live = rloc < a.nrows;
   const int iy = a.row_lo + rloc;
   const T2* tw = static_cast<const T2*>(a.tw);
@@ -354,16 +348,9 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_inv(Row
   }
   __syncthreads();
   if (live) {
-    size_t base = (size_t)c * a.n_act, stride = 1;
-    if (a.rhs_fast) {
-      const int pj = c / a.nrhs, r = c - pj * a.nrhs;
-      base = (size_t)pj * a.n_act * a.nrhs + r;
-      stride = (size_t)a.nrhs;
-    }
-    VT* out = static_cast<VT*>(a.vact) + base;
+    VT* out = static_cast<VT*>(a.vact) + (size_t)c * a.n_act;
     const int a1 = a.row_ptr[iy + 1];
-    for (int ap = a.row_ptr[iy] + rem; ap < a1; ap += per_row)
-      out[(size_t)ap * stride] = cto_vt(sm[fbA + padi<LOGE>(a.act_ix[ap])], sc);
+    for (int ap = a.row_ptr[iy] + rem; ap < a1; ap += per_row) out[ap] = cto_vt(sm[fbA + padi<LOGE>(a.act_ix[ap])], sc);
   }
 }
 
@@ -404,8 +391,7 @@ __global__ void k_gather(GatherArgs a) {
   for (int q = 0; q < kGatherRhs; ++q) re[q] = im[q] = 0.0;
   const int e0 = a.ga_ptr[i], e1 = a.ga_ptr[i + 1];
   for (int pj = 0; pj < a.nproj; ++pj) {
-    // restricted grid values, right-hand side fastest (for one right-hand side: n_act per channel)
-    const T2* v = static_cast<const T2*>(a.vact) + (size_t)pj * a.n_act * a.nrhs + r0;
+    const T2* v = static_cast<const T2*>(a.vact) + (size_t)(pj * a.nrhs + r0) * a.n_act;
     const double* w = a.w[pj];
     double cr[kGatherRhs], ci[kGatherRhs];
 #pragma unroll
@@ -416,7 +402,7 @@ __global__ void k_gather(GatherArgs a) {
 #pragma unroll
       for (int q = 0; q < kGatherRhs; ++q) {
         if (q < nr) {
-          const T2 val = v[(size_t)act * a.nrhs + q];
+          const T2 val = v[(size_t)q * a.n_act + act];
           cr[q] = fma(ww, (double)val.x, cr[q]);
           ci[q] = fma(ww, (double)val.y, ci[q]);
         }
@@ -565,7 +551,6 @@ static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdAr
          2 * rpc * LPT * tpf <= LaunchMax<CT, TPT, LOGE>::value)
     rpc *= 2;
   const int row_blocks = (ctx->nrows + rpc - 1) / rpc;
-  if (ia.rhs_fast && row_blocks > 65535) return fail(AIM_EINVAL, "too many grid rows for a batched pass");
   const size_t sm_row = 2 * (size_t)rpc * HS * sizeof(T2);
 
   fa.tw = tw;
@@ -616,8 +601,7 @@ static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdAr
   AIM_TRY(ensure_smem(k_row_inv<CT, TPT, LOGE>, sm_row));
   {
     ProfScope ps(K_ROW_INV, st);
-    const dim3 grid = ia.rhs_fast ? dim3(channels, row_blocks) : dim3(row_blocks, channels);
-    k_row_inv<CT, TPT, LOGE><<<grid, rpc * LPT * tpf, sm_row, st>>>(ia);
+    k_row_inv<CT, TPT, LOGE><<<dim3(row_blocks, channels), rpc * LPT * tpf, sm_row, st>>>(ia);
   }
   AIM_CUDA_TRY(cudaGetLastError());
   return AIM_OK;
@@ -671,8 +655,6 @@ aim_status grid_pass(aim_ctx* ctx, const PassSpec& spec, int nrhs, const double2
   ia.n_act = ctx->n_act;
   ia.row_ptr = ctx->row_ptr;
   ia.act_ix = ctx->act_ix;
-  ia.rhs_fast = nrhs > 1;
-  ia.nrhs = nrhs;
   AIM_TRY(launch_three_passes<CT>(ctx, channels, spec.filtered, fa, ia, st));
 
   GatherArgs ga{};
