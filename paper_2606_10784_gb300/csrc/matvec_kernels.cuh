@@ -373,81 +373,90 @@ struct GatherArgs {
   int accumulate;
 };
 
-// One warp per unknown i and block of up to kGatherRhs right-hand sides (1 when there is only
-// one): the CSR entries of row i (weights, active-point indices, near-field values and columns)
-// are loaded once and used for every right-hand side of the block. For each right-hand side the
-// lanes sum the entries e = lane, lane + 32, ... in order and then reduce by shuffles, so the
-// result does not depend on the block size.
+// A group of kGatherLanes adjacent lanes per unknown i and block of up to kGatherRhs right-hand
+// sides (1 when there is only one), four groups to a warp: the CSR entries of row i (weights,
+// active-point indices, near-field values and columns) are loaded once and used for every
+// right-hand side of the block. For each right-hand side, lane g of the group sums the entries
+// e = e0 + g, e0 + g + 8, ... in order, and the group then adds its partial sums by xor shuffles,
+// so the result does not depend on the block size. The FP64 pipe sets the cost here: a whole
+// warp per unknown spent more FP64 instructions on coefficient products and its five-step
+// shuffle tree than on the entries themselves.
+constexpr int kGatherLanes = 8;
+
 template <typename T2, int kGatherRhs>
 __global__ void k_gather(GatherArgs a) {
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
+  static_assert(kGatherRhs <= kGatherLanes, "lane g writes right-hand side r0 + g");
+  const long long grp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kGatherLanes;
+  const int g = threadIdx.x & (kGatherLanes - 1);
   const int nblk = (a.nrhs + kGatherRhs - 1) / kGatherRhs;
-  if (gw >= a.n * nblk) return;
-  const int rb = gw / a.n, i = gw - rb * a.n;
+  const bool valid = grp < (long long)a.n * nblk;
+  const int rb = valid ? (int)(grp / a.n) : 0, i = valid ? (int)(grp - (long long)rb * a.n) : 0;
   const int r0 = rb * kGatherRhs, nr = min(kGatherRhs, a.nrhs - r0);
   double re[kGatherRhs], im[kGatherRhs];
 #pragma unroll
   for (int q = 0; q < kGatherRhs; ++q) re[q] = im[q] = 0.0;
-  const int e0 = a.ga_ptr[i], e1 = a.ga_ptr[i + 1];
-  for (int pj = 0; pj < a.nproj; ++pj) {
-    const T2* v = static_cast<const T2*>(a.vact) + (size_t)(pj * a.nrhs + r0) * a.n_act;
-    const double* w = a.w[pj];
-    double cr[kGatherRhs], ci[kGatherRhs];
+  if (valid) {
+    const int e0 = a.ga_ptr[i], e1 = a.ga_ptr[i + 1];
+    for (int pj = 0; pj < a.nproj; ++pj) {
+      const T2* v = static_cast<const T2*>(a.vact) + (size_t)(pj * a.nrhs + r0) * a.n_act;
+      const double* w = a.w[pj];
+      double cr[kGatherRhs], ci[kGatherRhs];
 #pragma unroll
-    for (int q = 0; q < kGatherRhs; ++q) cr[q] = ci[q] = 0.0;
-    for (int e = e0 + lane; e < e1; e += 32) {
-      const double ww = w[e];
-      const int act = a.ga_act[e];
+      for (int q = 0; q < kGatherRhs; ++q) cr[q] = ci[q] = 0.0;
+      for (int e = e0 + g; e < e1; e += kGatherLanes) {
+        const double ww = w[e];
+        const int act = a.ga_act[e];
+#pragma unroll
+        for (int q = 0; q < kGatherRhs; ++q) {
+          if (q < nr) {
+            const T2 val = v[(size_t)q * a.n_act + act];
+            cr[q] = fma(ww, (double)val.x, cr[q]);
+            ci[q] = fma(ww, (double)val.y, ci[q]);
+          }
+        }
+      }
+      const double2 cf = a.coef[pj];
 #pragma unroll
       for (int q = 0; q < kGatherRhs; ++q) {
-        if (q < nr) {
-          const T2 val = v[(size_t)q * a.n_act + act];
-          cr[q] = fma(ww, (double)val.x, cr[q]);
-          ci[q] = fma(ww, (double)val.y, ci[q]);
+        re[q] += cf.x * cr[q] - cf.y * ci[q];
+        im[q] += cf.x * ci[q] + cf.y * cr[q];
+      }
+    }
+    if (a.nptr != nullptr) {
+      const T2* val = static_cast<const T2*>(a.nval);
+      const int n1 = a.nptr[i + 1];
+      for (int e = a.nptr[i] + g; e < n1; e += kGatherLanes) {
+        const T2 cv = val[e];
+        const int col = a.ncol[e];
+#pragma unroll
+        for (int q = 0; q < kGatherRhs; ++q) {
+          if (q < nr) {
+            const double2 xx = a.x[(size_t)(r0 + q) * a.n + col];
+            re[q] += (double)cv.x * xx.x - (double)cv.y * xx.y;
+            im[q] += (double)cv.x * xx.y + (double)cv.y * xx.x;
+          }
         }
       }
     }
-    const double2 cf = a.coef[pj];
-#pragma unroll
-    for (int q = 0; q < kGatherRhs; ++q) {
-      re[q] += cf.x * cr[q] - cf.y * ci[q];
-      im[q] += cf.x * ci[q] + cf.y * cr[q];
-    }
   }
-  if (a.nptr != nullptr) {
-    const T2* val = static_cast<const T2*>(a.nval);
-    const int n1 = a.nptr[i + 1];
-    for (int e = a.nptr[i] + lane; e < n1; e += 32) {
-      const T2 cv = val[e];
-      const int col = a.ncol[e];
-#pragma unroll
-      for (int q = 0; q < kGatherRhs; ++q) {
-        if (q < nr) {
-          const double2 xx = a.x[(size_t)(r0 + q) * a.n + col];
-          re[q] += (double)cv.x * xx.x - (double)cv.y * xx.y;
-          im[q] += (double)cv.x * xx.y + (double)cv.y * xx.x;
-        }
-      }
-    }
-  }
+  // every lane of the warp takes part in the shuffles (groups past the end carry zeros)
 #pragma unroll
   for (int q = 0; q < kGatherRhs; ++q) {
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
+    for (int off = kGatherLanes / 2; off > 0; off >>= 1) {
       re[q] += __shfl_xor_sync(0xffffffffu, re[q], off);
       im[q] += __shfl_xor_sync(0xffffffffu, im[q], off);
     }
   }
-  if (lane < nr) {
-    // lane q writes right-hand side r0 + q (select by unrolled compare: no local-memory indexing)
+  if (valid && g < nr) {
+    // lane g writes right-hand side r0 + g (select by unrolled compare: no local-memory indexing)
     double xr = 0.0, xi = 0.0;
 #pragma unroll
     for (int q = 0; q < kGatherRhs; ++q)
-      if (q == lane) { xr = re[q]; xi = im[q]; }
+      if (q == g) { xr = re[q]; xi = im[q]; }
     const double2 s = a.out_scale;
     double2 o = double2{s.x * xr - s.y * xi, s.x * xi + s.y * xr};
-    double2* dst = a.y + (size_t)(r0 + lane) * a.n + i;
+    double2* dst = a.y + (size_t)(r0 + g) * a.n + i;
     if (a.accumulate) {
       const double2 prev = *dst;
       o.x += prev.x;
@@ -680,9 +689,9 @@ aim_status grid_pass(aim_ctx* ctx, const PassSpec& spec, int nrhs, const double2
   ga.accumulate = 0;
   constexpr int kRhsBlock = 8;
   const int rb = nrhs == 1 ? 1 : kRhsBlock;
-  const long long warps = (long long)ctx->n * ((nrhs + rb - 1) / rb);
+  const long long groups = (long long)ctx->n * ((nrhs + rb - 1) / rb);
   const int tpb = 256;
-  const long long blocks = (warps * 32 + tpb - 1) / tpb;
+  const long long blocks = (groups * kGatherLanes + tpb - 1) / tpb;
   {
     ProfScope ps(K_GATHER, st);
     if (rb == 1)
