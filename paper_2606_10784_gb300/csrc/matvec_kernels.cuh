@@ -54,6 +54,8 @@ struct RowFwdArgs {
 };
 
 // CTA: rows_per_cta rows of one channel; (3 - TPT) * H/E threads per row (E = 2^LOGE elements each).
+constexpr int kAntChunk = 8;
+
 template <typename CT, int TPT, int LOGE>
 __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_fwd(RowFwdArgs a) {
   using T2 = CT;
@@ -73,7 +75,13 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_fwd(Row
   int fb[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) fb[f] = (2 * g + (TPT == 1 ? half : f)) * HS;
-  // zero the row buffer, then anterpolate u = P_s x into it
+  // zero the row buffer, then anterpolate u = P_s x into it (the row's active-point range is
+  // loaded first so that its latency overlaps the zeroing)
+  int a0 = 0, a1 = 0;
+  if (live && !a.dense) {
+    a0 = a.row_ptr[iy];
+    a1 = a.row_ptr[iy + 1];
+  }
   for (int i = rem; i < HS; i += per_row) sm[fbA + i] = czero<T2>();
   __syncthreads();
   if (live) {
@@ -87,15 +95,30 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_fwd(Row
       const int pj = c / a.nrhs, r = c - pj * a.nrhs;
       const double* w = a.w[pj];
       const double2* xv = a.x + (size_t)r * a.n;
-      const int a1 = a.row_ptr[iy + 1];
-      for (int ap = a.row_ptr[iy] + rem; ap < a1; ap += per_row) {
+      for (int ap = a0 + rem; ap < a1; ap += per_row) {
+        // a grid row holds few active points (tens), each with a handful of entries, so most of
+        // the CTA waits here: the loads of up to kAntChunk entries are issued together before
+        // their FMAs, which run in entry order as a plain loop would
         double re = 0.0, im = 0.0;
-        const int e1 = a.sc_ptr[ap + 1];
-        for (int e = a.sc_ptr[ap]; e < e1; ++e) {
-          const double ww = w[e];
-          const double2 xx = xv[a.sc_col[e]];
-          re = fma(ww, xx.x, re);
-          im = fma(ww, xx.y, im);
+        const int e0 = a.sc_ptr[ap], e1 = a.sc_ptr[ap + 1];
+        for (int e = e0; e < e1; e += kAntChunk) {
+          int col[kAntChunk];
+          double ww[kAntChunk];
+          double2 xx[kAntChunk];
+#pragma unroll
+          for (int u = 0; u < kAntChunk; ++u) {
+            col[u] = e + u < e1 ? a.sc_col[e + u] : 0;
+            ww[u] = e + u < e1 ? w[e + u] : 0.0;
+          }
+#pragma unroll
+          for (int u = 0; u < kAntChunk; ++u) xx[u] = e + u < e1 ? xv[col[u]] : double2{0.0, 0.0};
+#pragma unroll
+          for (int u = 0; u < kAntChunk; ++u) {
+            if (e + u < e1) {
+              re = fma(ww[u], xx[u].x, re);
+              im = fma(ww[u], xx[u].y, im);
+            }
+          }
         }
         sm[fbA + padi<LOGE>(a.act_ix[ap])] = cfrom<T2>(re, im);
       }
