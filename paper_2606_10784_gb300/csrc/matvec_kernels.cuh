@@ -93,7 +93,12 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_fwd(Row
       }
     } else {
       const int pj = c / a.nrhs, r = c - pj * a.nrhs;
-      const double* w = a.w[pj];
+      // projection weights by unrolled compare (indexing the argument array with a runtime
+      // index would copy it to local memory)
+      const double* w = a.w[0];
+#pragma unroll
+      for (int q = 1; q < kMaxProj; ++q)
+        if (q == pj) w = a.w[q];
       const double2* xv = a.x + (size_t)r * a.n;
       for (int ap = a0 + rem; ap < a1; ap += per_row) {
         // a grid row holds few active points (tens), each with a handful of entries, so most of
