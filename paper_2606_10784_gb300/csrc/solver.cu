@@ -130,14 +130,9 @@ __global__ void k_to_dfc(const double2* __restrict__ src, int count, dfc* __rest
 
 // Double-float form of k_multidot_partial: part[(z J + j) nrhs + r] = sum over chunk z of
 // conj(V[j][r][i]) w[r][i], products and per-thread sums in double-float, block sum in FP64.
-// only (may be null): right-hand sides whose flag is 0 get zero partials without reading V.
 __global__ void k_multidot_partial_df(const dfc* __restrict__ V, const dfc* __restrict__ w, int n, int nrhs, int J,
-                                      double2* __restrict__ part, const int* __restrict__ only) {
+                                      double2* __restrict__ part) {
   const int j = blockIdx.x, r = blockIdx.y, z = blockIdx.z;
-  if (only != nullptr && only[r] == 0) {   // uniform over the block
-    if (threadIdx.x == 0) part[((size_t)z * J + j) * nrhs + r] = double2{0.0, 0.0};
-    return;
-  }
   const int i0 = z * kDotChunk, i1 = min(n, i0 + kDotChunk);
   const dfc* v = V + ((size_t)j * nrhs + r) * n;
   const dfc* x = w + (size_t)r * n;
@@ -190,16 +185,11 @@ __global__ void k_multidot_finish_df(const double2* __restrict__ part, int nz, i
 }
 
 // Stage 1 of the basis update: part[chunk][r][i] = sum over the chunk of V[j][r][i] c[j*nrhs + r]
-// (zero without reading V for a right-hand side whose flag in `only` is 0)
 __global__ void k_vcombine_partial_df(const dfc* __restrict__ V, const dfc* __restrict__ c, int J, int n, int nrhs,
-                                      double2* __restrict__ part, const int* __restrict__ only) {
+                                      double2* __restrict__ part) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int chunk = blockIdx.y, r = blockIdx.z;
   if (i >= n) return;
-  if (only != nullptr && only[r] == 0) {
-    part[((size_t)chunk * nrhs + r) * n + i] = double2{0.0, 0.0};
-    return;
-  }
   const int j0 = chunk * kCgsChunk, j1 = min(J, j0 + kCgsChunk);
   float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
   for (int j = j0; j < j1; ++j) {
@@ -229,16 +219,6 @@ __global__ void k_vcombine_finish_df(const double2* __restrict__ part, int nchun
   const double2 o = double2{out[t].x + sign * re, out[t].y + sign * im};
   out[t] = o;
   if (out_df != nullptr) out_df[t] = to_dfc(o);
-}
-
-// Selective reorthogonalisation, the criterion of Daniel, Gragg, Kaufman and Stewart (1976): the
-// second classical Gram-Schmidt pass runs for right-hand side r only if the first one removed more
-// than half of the squared norm of w (||w'||^2 < ||w||^2 / 2). Otherwise w' is already orthogonal
-// to the basis to working precision, and a skipped pass contributes exact zeros.
-__global__ void k_reorth_flags(const double2* __restrict__ before, const double2* __restrict__ after, int nrhs,
-                               int* __restrict__ flags) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r < nrhs) flags[r] = after[r].x < 0.5 * before[r].x ? 1 : 0;
 }
 
 __global__ void k_add_small(double2* a, const double2* b, int count) {
@@ -282,10 +262,9 @@ inline double cabs2(Zc a) { return a.re * a.re + a.im * a.im; }
 
 struct Workspace {
   dfc* V;                      // basis, double-float
-  double2 *w, *r, *cur, *tmp, *dots, *dots2, *nrm, *nrm0, *nrm1;
+  double2 *w, *r, *cur, *tmp, *dots, *dots2, *nrm;
   dfc *wdf, *dots_df, *dots2_df;
   int* active;
-  int* reorth;                 // per rhs: 1 if this step runs the second Gram-Schmidt pass
 };
 
 inline int blocks_for(long long total, int tpb) { return (int)((total + tpb - 1) / tpb); }
@@ -363,10 +342,10 @@ struct OpGraph {
 
 // out[j*nrhs + r] = <V[j][r], w[r]> for j < J over the double-float basis (two launches)
 static aim_status multidot_df(const dfc* V, const dfc* w, int J, int n, int nrhs, double2* out, dfc* out_df,
-                              double2* part, cudaStream_t st, const int* only = nullptr) {
+                              double2* part, cudaStream_t st) {
   const int nz = (n + kDotChunk - 1) / kDotChunk;
   count_launches(K_GMRES, 2);
-  k_multidot_partial_df<<<dim3(J, nrhs, nz), 256, 0, st>>>(V, w, n, nrhs, J, part, only);
+  k_multidot_partial_df<<<dim3(J, nrhs, nz), 256, 0, st>>>(V, w, n, nrhs, J, part);
   k_multidot_finish_df<<<blocks_for((long long)J * nrhs, 256), 256, 0, st>>>(part, nz, J * nrhs, out, out_df);
   AIM_CUDA_TRY(cudaGetLastError());
   return AIM_OK;
@@ -374,10 +353,10 @@ static aim_status multidot_df(const dfc* V, const dfc* w, int J, int n, int nrhs
 
 // out += sign * V c over J vectors of the double-float basis (two launches, deterministic order)
 static void vcombine_df(const dfc* V, const dfc* c, int J, int n, int nrhs, double sign, double2* out, dfc* out_df,
-                        double2* part, cudaStream_t st, const int* only = nullptr) {
+                        double2* part, cudaStream_t st) {
   const int nch = (J + kCgsChunk - 1) / kCgsChunk;
   count_launches(K_GMRES, 2);
-  k_vcombine_partial_df<<<dim3((n + 255) / 256, nch, nrhs), 256, 0, st>>>(V, c, J, n, nrhs, part, only);
+  k_vcombine_partial_df<<<dim3((n + 255) / 256, nch, nrhs), 256, 0, st>>>(V, c, J, n, nrhs, part);
   k_vcombine_finish_df<<<(n * nrhs + 255) / 256, 256, 0, st>>>(part, nch, n, nrhs, sign, out, out_df);
 }
 
@@ -399,8 +378,8 @@ static aim_status ensure_krylov(aim_ctx* ctx, int nrhs, int restart) {
     ctx->kry = static_cast<double2*>(p);
     ctx->kry_bytes = need;
   }
-  // dots, dots2, norms, their double-float copies, the active and the reorthogonalisation flags
-  const size_t rneed = ((size_t)(restart + 2) * 5 + 1) * nrhs * sizeof(double2) + 2 * nrhs * sizeof(int);
+  // dots, dots2, norms, their double-float copies, and the active flags
+  const size_t rneed = ((size_t)(restart + 2) * 5 + 1) * nrhs * sizeof(double2) + nrhs * sizeof(int);
   if (ctx->red_bytes < rneed) {
     if (ctx->red) cudaFree(ctx->red);
     if (ctx->red_host) cudaFreeHost(ctx->red_host);
@@ -443,12 +422,9 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
   ws.dots = red;                                   // (restart+1) * nrhs
   ws.dots2 = red + (size_t)(restart + 2) * nrhs;   // (restart+1) * nrhs
   ws.nrm = red + (size_t)(restart + 2) * 2 * nrhs; // nrhs
-  ws.nrm0 = ws.nrm + nrhs;                         // nrhs: ||w||^2 before the first pass
-  ws.nrm1 = ws.nrm + 2 * nrhs;                     // nrhs: after it (restart + 2 >= 3 slots)
   ws.dots_df = reinterpret_cast<dfc*>(red + (size_t)(restart + 2) * 3 * nrhs);   // (restart+1) * nrhs
   ws.dots2_df = reinterpret_cast<dfc*>(red + (size_t)(restart + 2) * 4 * nrhs);  // (restart+1) * nrhs
   ws.active = reinterpret_cast<int*>(red + ((size_t)(restart + 2) * 5 + 1) * nrhs);
-  ws.reorth = ws.active + nrhs;
   double2* hred = reinterpret_cast<double2*>(ctx->red_host);
   const int tpb = 256;
   const int nb = blocks_for((long long)vsz, tpb);
@@ -521,18 +497,15 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
       } else {
         AIM_TRY(apply_op(ctx, op, nrhs, ws.cur, ws.w, precision, st));
       }
-      // classical Gram-Schmidt with a selective second pass (4 launches here + 2 x 2 in
-      // multidot_df + 2 x 2 in vcombine_df + 3 x 2 in dot_norms), timed as one group when profiling
+      // CGS2 (3 launches here + 2 x 2 in multidot_df + 2 x 2 in vcombine_df + 2 in dot_norms),
+      // timed as one group when profiling
       ProfScope group(K_GMRES, st, /*count_launch=*/false);
-      count_launches(K_GMRES, 4);
+      count_launches(K_GMRES, 3);
       k_to_dfc<<<nb, tpb, 0, st>>>(ws.w, (int)vsz, ws.wdf);
-      AIM_TRY(dot_norms(ws.w, n, nrhs, ws.nrm0, ws.tmp, st));
       AIM_TRY(multidot_df(ws.V, ws.wdf, j + 1, n, nrhs, ws.dots, ws.dots_df, ws.tmp, st));
       vcombine_df(ws.V, ws.dots_df, j + 1, n, nrhs, -1.0, ws.w, ws.wdf, ws.tmp, st);
-      AIM_TRY(dot_norms(ws.w, n, nrhs, ws.nrm1, ws.tmp, st));
-      k_reorth_flags<<<blocks_for(nrhs, tpb), tpb, 0, st>>>(ws.nrm0, ws.nrm1, nrhs, ws.reorth);
-      AIM_TRY(multidot_df(ws.V, ws.wdf, j + 1, n, nrhs, ws.dots2, ws.dots2_df, ws.tmp, st, ws.reorth));
-      vcombine_df(ws.V, ws.dots2_df, j + 1, n, nrhs, -1.0, ws.w, nullptr, ws.tmp, st, ws.reorth);
+      AIM_TRY(multidot_df(ws.V, ws.wdf, j + 1, n, nrhs, ws.dots2, ws.dots2_df, ws.tmp, st));
+      vcombine_df(ws.V, ws.dots2_df, j + 1, n, nrhs, -1.0, ws.w, nullptr, ws.tmp, st);
       k_add_small<<<blocks_for((j + 1) * nrhs, tpb), tpb, 0, st>>>(ws.dots, ws.dots2, (j + 1) * nrhs);
       AIM_TRY(dot_norms(ws.w, n, nrhs, ws.nrm, ws.tmp, st));
       k_normalize<<<nb, tpb, 0, st>>>(ws.w, ws.nrm, ws.active, n, nrhs, ws.V + (size_t)(j + 1) * vsz, ws.cur);
