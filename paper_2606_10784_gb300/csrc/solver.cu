@@ -128,8 +128,20 @@ __global__ void k_to_dfc(const double2* __restrict__ src, int count, dfc* __rest
   if (t < count) dst[t] = to_dfc(src[t]);
 }
 
+// Sum of a complex double-float value over the 32 lanes of a warp (fixed xor tree: every lane
+// ends with the same, deterministic result)
+__device__ __forceinline__ void warp_sum_df(float& rh, float& rl, float& ih, float& il) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const float orh = __shfl_xor_sync(0xffffffffu, rh, off), orl = __shfl_xor_sync(0xffffffffu, rl, off);
+    const float oih = __shfl_xor_sync(0xffffffffu, ih, off), oil = __shfl_xor_sync(0xffffffffu, il, off);
+    df_add(rh, rl, orh, orl, rh, rl);
+    df_add(ih, il, oih, oil, ih, il);
+  }
+}
+
 // Double-float form of k_multidot_partial: part[(z J + j) nrhs + r] = sum over chunk z of
-// conj(V[j][r][i]) w[r][i], products and per-thread sums in double-float, block sum in FP64.
+// conj(V[j][r][i]) w[r][i], products, per-thread and block sums in double-float.
 __global__ void k_multidot_partial_df(const dfc* __restrict__ V, const dfc* __restrict__ w, int n, int nrhs, int J,
                                       double2* __restrict__ part) {
   const int j = blockIdx.x, r = blockIdx.y, z = blockIdx.z;
@@ -145,27 +157,26 @@ __global__ void k_multidot_partial_df(const dfc* __restrict__ V, const dfc* __re
     df_dot2<-1>(a.xh, a.xl, b.yh, b.yl, a.yh, a.yl, b.xh, b.xl, ph, pl);   // ax by - ay bx
     df_add(ih, il, ph, pl, ih, il);
   }
-  const double2 acc = to_d2(rh, rl, ih, il);
-  double re = acc.x, im = acc.y;
-  __shared__ double sre[32], sim[32];
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) {
-    re += __shfl_xor_sync(0xffffffffu, re, off);
-    im += __shfl_xor_sync(0xffffffffu, im, off);
-  }
+  // warp and block sums in double-float as well: on this part FP64 runs at 1/64 of the FP32
+  // rate, and an FP64 shuffle tree per block cost about as much time as reading the basis
+  __shared__ float s4[32][4];
+  warp_sum_df(rh, rl, ih, il);
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) { sre[wid] = re; sim[wid] = im; }
+  if (lane == 0) {
+    s4[wid][0] = rh;
+    s4[wid][1] = rl;
+    s4[wid][2] = ih;
+    s4[wid][3] = il;
+  }
   __syncthreads();
   if (wid == 0) {
     const int nw = blockDim.x >> 5;
-    re = lane < nw ? sre[lane] : 0.0;
-    im = lane < nw ? sim[lane] : 0.0;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      re += __shfl_xor_sync(0xffffffffu, re, off);
-      im += __shfl_xor_sync(0xffffffffu, im, off);
-    }
-    if (lane == 0) part[((size_t)z * J + j) * nrhs + r] = double2{re, im};
+    rh = lane < nw ? s4[lane][0] : 0.f;
+    rl = lane < nw ? s4[lane][1] : 0.f;
+    ih = lane < nw ? s4[lane][2] : 0.f;
+    il = lane < nw ? s4[lane][3] : 0.f;
+    warp_sum_df(rh, rl, ih, il);
+    if (lane == 0) part[((size_t)z * J + j) * nrhs + r] = to_d2(rh, rl, ih, il);
   }
 }
 
