@@ -195,9 +195,11 @@ __global__ void k_multidot_finish_df(const double2* __restrict__ part, int nz, i
   out_df[t] = to_dfc(double2{re, im});
 }
 
-// Stage 1 of the basis update: part[chunk][r][i] = sum over the chunk of V[j][r][i] c[j*nrhs + r]
+// Stage 1 of the basis update: part[chunk][r][i] = sum over the chunk of V[j][r][i] c[j*nrhs + r],
+// kept in double-float (converting every chunk sum to FP64 and adding them on the FP64 pipe, at
+// 1/64 of the FP32 rate here, cost more than the additions in double-float)
 __global__ void k_vcombine_partial_df(const dfc* __restrict__ V, const dfc* __restrict__ c, int J, int n, int nrhs,
-                                      double2* __restrict__ part) {
+                                      dfc* __restrict__ part) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int chunk = blockIdx.y, r = blockIdx.z;
   if (i >= n) return;
@@ -212,22 +214,28 @@ __global__ void k_vcombine_partial_df(const dfc* __restrict__ V, const dfc* __re
     df_dot2<+1>(v.xh, v.xl, h.yh, h.yl, v.yh, v.yl, h.xh, h.xl, ph, pl);   // vx hy + vy hx
     df_add(ih, il, ph, pl, ih, il);
   }
-  part[((size_t)chunk * nrhs + r) * n + i] = to_d2(rh, rl, ih, il);
+  dfc o;
+  o.xh = rh;
+  o.xl = rl;
+  o.yh = ih;
+  o.yl = il;
+  part[((size_t)chunk * nrhs + r) * n + i] = o;
 }
 
-// Stage 2: out += sign * sum of the chunk partials (FP64, in chunk order); out_df (may be null)
-// receives the double-float copy of the updated out
-__global__ void k_vcombine_finish_df(const double2* __restrict__ part, int nchunks, int n, int nrhs, double sign,
+// Stage 2: out += sign * sum of the chunk partials (double-float, in chunk order, then FP64);
+// out_df (may be null) receives the double-float copy of the updated out
+__global__ void k_vcombine_finish_df(const dfc* __restrict__ part, int nchunks, int n, int nrhs, double sign,
                                      double2* __restrict__ out, dfc* __restrict__ out_df) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * nrhs) return;
-  double re = 0.0, im = 0.0;
+  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
   for (int ch = 0; ch < nchunks; ++ch) {
-    const double2 p = part[(size_t)ch * n * nrhs + t];
-    re += p.x;
-    im += p.y;
+    const dfc p = part[(size_t)ch * n * nrhs + t];
+    df_add(rh, rl, p.xh, p.xl, rh, rl);
+    df_add(ih, il, p.yh, p.yl, ih, il);
   }
-  const double2 o = double2{out[t].x + sign * re, out[t].y + sign * im};
+  const double2 sum = to_d2(rh, rl, ih, il);
+  const double2 o = double2{out[t].x + sign * sum.x, out[t].y + sign * sum.y};
   out[t] = o;
   if (out_df != nullptr) out_df[t] = to_dfc(o);
 }
@@ -367,8 +375,9 @@ static void vcombine_df(const dfc* V, const dfc* c, int J, int n, int nrhs, doub
                         double2* part, cudaStream_t st) {
   const int nch = (J + kCgsChunk - 1) / kCgsChunk;
   count_launches(K_GMRES, 2);
-  k_vcombine_partial_df<<<dim3((n + 255) / 256, nch, nrhs), 256, 0, st>>>(V, c, J, n, nrhs, part);
-  k_vcombine_finish_df<<<(n * nrhs + 255) / 256, 256, 0, st>>>(part, nch, n, nrhs, sign, out, out_df);
+  dfc* part_df = reinterpret_cast<dfc*>(part);   // same 16-byte elements
+  k_vcombine_partial_df<<<dim3((n + 255) / 256, nch, nrhs), 256, 0, st>>>(V, c, J, n, nrhs, part_df);
+  k_vcombine_finish_df<<<(n * nrhs + 255) / 256, 256, 0, st>>>(part_df, nch, n, nrhs, sign, out, out_df);
 }
 
 static aim_status ensure_krylov(aim_ctx* ctx, int nrhs, int restart) {
