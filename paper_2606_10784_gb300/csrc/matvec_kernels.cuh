@@ -75,21 +75,25 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_fwd(Row
   int fb[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) fb[f] = (2 * g + (TPT == 1 ? half : f)) * HS;
-  // zero the row buffer, then anterpolate u = P_s x into it (the row's active-point range is
-  // loaded first so that its latency overlaps the zeroing)
+  // zero the row's two buffers, then anterpolate u = P_s x into the first and u w^n into the
+  // second (the row's active-point range is loaded first so that its latency overlaps the
+  // zeroing). Forming u w^n here, at the few active points of the row, spares pass 0 a product
+  // and a twiddle load for each of the H points of the odd half.
   int a0 = 0, a1 = 0;
   if (live && !a.dense) {
     a0 = a.row_ptr[iy];
     a1 = a.row_ptr[iy + 1];
   }
-  for (int i = rem; i < HS; i += per_row) sm[fbA + i] = czero<T2>();
+  for (int i = rem; i < 2 * HS; i += per_row) sm[fbA + i] = czero<T2>();
   __syncthreads();
   if (live) {
     if (a.dense) {
       const double2* u = a.x + (size_t)c * a.m * a.m + (size_t)iy * a.m;
       for (int ix = rem; ix < a.m; ix += per_row) {
         const double2 v = u[ix];
-        sm[fbA + padi<LOGE>(ix)] = cfrom<T2>(v.x, v.y);
+        const T2 x = cfrom<T2>(v.x, v.y);
+        sm[fbA + padi<LOGE>(ix)] = x;
+        sm[fbA + HS + padi<LOGE>(ix)] = cmul(x, ldro(&tw[ix]));
       }
     } else {
       const int pj = c / a.nrhs, r = c - pj * a.nrhs;
@@ -125,24 +129,24 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_fwd(Row
             }
           }
         }
-        sm[fbA + padi<LOGE>(a.act_ix[ap])] = cfrom<T2>(re, im);
+        const int ix = a.act_ix[ap];
+        const T2 x = cfrom<T2>(re, im);
+        sm[fbA + padi<LOGE>(ix)] = x;
+        sm[fbA + HS + padi<LOGE>(ix)] = cmul(x, ldro(&tw[ix]));
       }
     }
   }
   __syncthreads();
-  // pass 0 (radix E, Ns = 1): the transform of a and/or of a w^n
+  // pass 0 (radix E, Ns = 1): the transform of a and/or of a w^n, each from its own buffer
   {
     const int lognb = a.logH - LOGE;
     T2 v[NF][1 << LOGE];
 #pragma unroll
-    for (int r = 0; r < (1 << LOGE); ++r) {
-      const int nn = j + (r << lognb);
-      const T2 x = sm[fbA + padi<LOGE>(nn)];
+    for (int f = 0; f < NF; ++f) {
 #pragma unroll
-      for (int f = 0; f < NF; ++f) v[f][r] = (TPT == 1 ? half : f) ? cmul(x, ldro(&tw[nn])) : x;
+      for (int r = 0; r < (1 << LOGE); ++r) v[f][r] = sm[fbA + (TPT == 1 ? half : f) * HS + padi<LOGE>(j + (r << lognb))];
+      dft_reg<(1 << LOGE), false>(v[f]);
     }
-#pragma unroll
-    for (int f = 0; f < NF; ++f) dft_reg<(1 << LOGE), false>(v[f]);
     __syncthreads();
 #pragma unroll
     for (int f = 0; f < NF; ++f)
@@ -354,31 +358,18 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_inv(Row
     });
     return;
   }
-  // sparse mode: results into registers, then through shared memory to the active points
-  T2 ybuf[1 << LOGE];
-  int ycnt = 0;
-  last_pass_dispatch<true, NF, LOGE>(sm, fb, j, tpf, a.logH, logNs, tw, a.logP, [&](int nn, const T2 (&v)[NF]) {
-    ybuf[ycnt++ & ((1 << LOGE) - 1)] = recombine<TPT>(v, half, tw, nn);
-  });
-  __syncthreads();
-  if (!half) {
-    // replay the output indices of the last pass to place the recombined values
-    const int lr = fft_logr<LOGE>(np - 1, a.logH);
-    const int R = 1 << lr, NB = (1 << LOGE) >> lr;
-    const int nsm = (1 << logNs) - 1;
-    int q = 0;
-    for (int t = 0; t < NB; ++t) {
-      const int b = j + t * tpf;
-      const int k = b & nsm;
-      const int base = ((b - k) << lr) + k;
-      for (int r = 0; r < R; ++r) sm[fbA + padi<LOGE>(base + (r << logNs))] = ybuf[q++];
-    }
-  }
-  __syncthreads();
+  // sparse mode: the last pass as one more shared-memory pass leaves both half-transforms in
+  // natural order in their own buffers, and the recombination y = Y_even + w^-n Y_odd runs only
+  // at the row's active points (tens of the H outputs)
+  smem_passes<true, NF, LOGE>(sm, fb, j, tpf, a.logH, np - 1, np, logNs, tw, a.logP, Identity{});
   if (live) {
     VT* out = static_cast<VT*>(a.vact) + (size_t)c * a.n_act;
     const int a1 = a.row_ptr[iy + 1];
-    for (int ap = a.row_ptr[iy] + rem; ap < a1; ap += per_row) out[ap] = cto_vt(sm[fbA + padi<LOGE>(a.act_ix[ap])], sc);
+    for (int ap = a.row_ptr[iy] + rem; ap < a1; ap += per_row) {
+      const int ix = a.act_ix[ap];
+      const T2 y = cadd(sm[fbA + padi<LOGE>(ix)], cmulc(sm[fbA + HS + padi<LOGE>(ix)], ldro(&tw[ix])));
+      out[ap] = cto_vt(y, sc);
+    }
   }
 }
 
