@@ -397,12 +397,16 @@ struct GatherArgs {
 // e = e0 + g, e0 + g + 8, ... in order, and the group then adds its partial sums by xor shuffles,
 // so the result does not depend on the block size. The FP64 pipe sets the cost here: a whole
 // warp per unknown spent more FP64 instructions on coefficient products and its five-step
-// shuffle tree than on the entries themselves.
+// shuffle tree than on the entries themselves. With a complex64 grid (mixed precision) the
+// projection sums run in FP32 (Acc): converting every grid value to FP64 cost as much as the
+// FP64 products, conversions running at the FP64 rate here. The coefficient products, the
+// near-field rows and the sums over projections stay in FP64.
 constexpr int kGatherLanes = 8;
 
 template <typename T2, int kGatherRhs>
 __global__ void k_gather(GatherArgs a) {
   static_assert(kGatherRhs <= kGatherLanes, "lane g writes right-hand side r0 + g");
+  using Acc = typename std::conditional<std::is_same<T2, float2>::value, float, double>::type;
   const long long grp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kGatherLanes;
   const int g = threadIdx.x & (kGatherLanes - 1);
   const int nblk = (a.nrhs + kGatherRhs - 1) / kGatherRhs;
@@ -417,26 +421,27 @@ __global__ void k_gather(GatherArgs a) {
     for (int pj = 0; pj < a.nproj; ++pj) {
       const T2* v = static_cast<const T2*>(a.vact) + (size_t)(pj * a.nrhs + r0) * a.n_act;
       const double* w = a.w[pj];
-      double cr[kGatherRhs], ci[kGatherRhs];
+      Acc cr[kGatherRhs], ci[kGatherRhs];
 #pragma unroll
-      for (int q = 0; q < kGatherRhs; ++q) cr[q] = ci[q] = 0.0;
+      for (int q = 0; q < kGatherRhs; ++q) cr[q] = ci[q] = Acc(0);
       for (int e = e0 + g; e < e1; e += kGatherLanes) {
-        const double ww = w[e];
+        const Acc ww = static_cast<Acc>(w[e]);
         const int act = a.ga_act[e];
 #pragma unroll
         for (int q = 0; q < kGatherRhs; ++q) {
           if (q < nr) {
             const T2 val = v[(size_t)q * a.n_act + act];
-            cr[q] = fma(ww, (double)val.x, cr[q]);
-            ci[q] = fma(ww, (double)val.y, ci[q]);
+            cr[q] = fma(ww, static_cast<Acc>(val.x), cr[q]);
+            ci[q] = fma(ww, static_cast<Acc>(val.y), ci[q]);
           }
         }
       }
       const double2 cf = a.coef[pj];
 #pragma unroll
       for (int q = 0; q < kGatherRhs; ++q) {
-        re[q] += cf.x * cr[q] - cf.y * ci[q];
-        im[q] += cf.x * ci[q] + cf.y * cr[q];
+        const double crq = cr[q], ciq = ci[q];
+        re[q] += cf.x * crq - cf.y * ciq;
+        im[q] += cf.x * ciq + cf.y * crq;
       }
     }
     if (a.nptr != nullptr) {
