@@ -80,12 +80,10 @@ struct Projections {
   int* sc_ptr = nullptr;   // n_act + 1
   int* sc_col = nullptr;   // hat / segment index
   double* sc_w[kMaxProj] = {};
-  float* sc_wf[kMaxProj] = {};
   // gather side, unknown-major CSR: y[i] = sum w * v[act]
   int* ga_ptr = nullptr;   // n + 1
   int* ga_act = nullptr;   // active point index
   double* ga_w[kMaxProj] = {};
-  float* ga_wf[kMaxProj] = {};
   int nproj = 0;
 };
 
