@@ -98,6 +98,17 @@ __device__ __forceinline__ void df_split(double d, float& h, float& l) {
 __host__ __device__ constexpr float df_hi(double d) { return (float)d; }
 __host__ __device__ constexpr float df_lo(double d) { return (float)(d - (double)(float)d); }
 
+// (ah + al) * c for a double-float constant c = ch + cl (exact product of the high parts by FMA,
+// cross terms added to the low part; unnormalised like df_add)
+__device__ __forceinline__ void df_scale(float ah, float al, float ch, float cl, float& rh, float& rl) {
+  const float p = __fmul_rn(ah, ch);
+  float e = __fmaf_rn(ah, ch, -p);
+  e = __fmaf_rn(ah, cl, e);
+  e = __fmaf_rn(al, ch, e);
+  rh = p;
+  rl = e;
+}
+
 // d * W16^e with double-float constants (forward W16 = exp(-2 pi i/16); inverse conjugate)
 template <bool INV>
 __device__ __forceinline__ dfc rot16(dfc d, int e) {
@@ -105,6 +116,27 @@ __device__ __forceinline__ dfc rot16(dfc d, int e) {
   switch (e) {
     case 0: return d;
     case 4: return INV ? mul_plus_i(d) : mul_minus_i(d);
+    case 2:
+    case 6: {
+      // W8 and W8^3 have |re| = |im| = 1/sqrt2: two sums and two scalings (24 FP32 operations)
+      // instead of a full complex product (32). With x + iy = d:
+      //   forward e = 2: c (x + y) + i c (y - x)      inverse e = 2: c (x - y) + i c (x + y)
+      //   forward e = 6: c (y - x) - i c (x + y)      inverse e = 6: -c (x + y) + i c (x - y)
+      constexpr float ch = df_hi(C2), cl = df_lo(C2);
+      float ph, pl, mh, ml;   // p = x + y, m = y - x (forward) or x - y (inverse)
+      df_add(d.xh, d.xl, d.yh, d.yl, ph, pl);
+      if (INV) df_add(d.xh, d.xl, -d.yh, -d.yl, mh, ml);
+      else df_add(d.yh, d.yl, -d.xh, -d.xl, mh, ml);
+      dfc r;
+      if (e == 2) {
+        if (INV) { df_scale(mh, ml, ch, cl, r.xh, r.xl); df_scale(ph, pl, ch, cl, r.yh, r.yl); }
+        else { df_scale(ph, pl, ch, cl, r.xh, r.xl); df_scale(mh, ml, ch, cl, r.yh, r.yl); }
+      } else {
+        if (INV) { df_scale(ph, pl, -ch, -cl, r.xh, r.xl); df_scale(mh, ml, ch, cl, r.yh, r.yl); }
+        else { df_scale(mh, ml, ch, cl, r.xh, r.xl); df_scale(ph, pl, -ch, -cl, r.yh, r.yl); }
+      }
+      return r;
+    }
     default: {
       double c, s;
       switch (e) {
