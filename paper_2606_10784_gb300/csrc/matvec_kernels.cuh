@@ -211,16 +211,19 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_col_conv(Co
   const int r2 = TPT == 1 ? (rem >> 1) : rem;
   const int wl = r2 & (cw - 1), j = r2 / cw;
   const int colc = g * cw + wl;                         // column within the CTA
-  const int qcol = (blockIdx.x << a.log_cols) + colc;   // column of the grid
+  // channels run along x: the channels of one column tile run back to back, so the spectrum
+  // column they share comes from DRAM once and from L2 for the others
+  const int ctile = blockIdx.y;
+  const int qcol = (ctile << a.log_cols) + colc;   // column of the grid
   const int w = qcol & (W - 1), tile = qcol / W;
-  const int c = blockIdx.y;
+  const int c = blockIdx.x;
   if (a.live != nullptr) {
     // the filtered spectrum (Eq. 10) vanishes on columns beyond the mask radius: when it does on
     // every column of this CTA their product is zero, so write zeros and skip the transforms
     // (the same decision in every thread: the early return is uniform)
     bool any = false;
     for (int cc = 0; cc < (1 << a.log_cols); ++cc) {
-      const int q = (blockIdx.x << a.log_cols) + cc;
+      const int q = (ctile << a.log_cols) + cc;
       any = any || a.live[min(q, P - q)] != 0;
     }
     if (!any) {
@@ -228,7 +231,7 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_col_conv(Co
       const int total = (1 << a.log_cols) * a.nrows;
       for (int e = threadIdx.x; e < total; e += blockDim.x) {
         const int cc = e / a.nrows, row = e - cc * a.nrows;
-        const int q = (blockIdx.x << a.log_cols) + cc;
+        const int q = (ctile << a.log_cols) + cc;
         base[((size_t)(q / W) * a.nrows + row) * W + (q & (W - 1))] = czero<T2>();
       }
       return;
@@ -613,10 +616,11 @@ static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdAr
   ca.nrows = ctx->nrows;
   ca.log_cols = log_cols;
   const size_t sm_col = 2 * (size_t)cols * HS * sizeof(T2);
+  if (ctx->P / cols > 65535) return fail(AIM_EINVAL, "too many column tiles for one column-pass grid");
   AIM_TRY(ensure_smem(k_col_conv<CT, TPT, LOGE>, sm_col));
   {
     ProfScope ps(K_COL_CONV, st);
-    k_col_conv<CT, TPT, LOGE><<<dim3(ctx->P / cols, channels), cols * LPT * tpf, sm_col, st>>>(ca);
+    k_col_conv<CT, TPT, LOGE><<<dim3(channels, ctx->P / cols), cols * LPT * tpf, sm_col, st>>>(ca);
   }
   AIM_CUDA_TRY(cudaGetLastError());
 
