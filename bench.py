@@ -199,7 +199,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x 
 # the two launches of one filtered Calderon product (N: 3 channels, S^alpha: 1 channel), from one
 # ncu capture of the default schedule at the single-solve size; the profiles directory gives the
 # capture and its command. None where no capture matches the current kernel and schedule.
-COL_CONV_TRAFFIC = {"fp64": 534150784, "mixed": 202739328, "native": None}
+COL_CONV_TRAFFIC = {"fp64": 531852928, "mixed": 202739328, "native": None}
 
 
 def aggregate(elapsed: float, steps: int, world: int, device=None):
