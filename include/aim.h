@@ -80,9 +80,10 @@ typedef enum {
 
 /* Grid arithmetic of a product (vectors are complex128 in every mode):
  *   AIM_FP64        FP64-accurate (relative rounding ~2^-48 per operation): double-float
- *                   arithmetic on the FP32 pipe, since GB300's FP64 pipe is ~1/58 of its FP32
+ *                   arithmetic on the FP32 pipe, since GB300's FP64 pipe is ~1/64 of its FP32
  *                   pipe; grid intermediates are 16 bytes per complex.
- *   AIM_MIXED       complex64 grid products and near-field SpMV (FP32 arithmetic).
+ *   AIM_MIXED       complex64 grid products and interpolation sums (FP32 arithmetic); near-field
+ *                   values stored as complex64 and applied with FP64 sums.
  *   AIM_FP64_NATIVE IEEE binary64 grid arithmetic on the FP64 pipe (the reference the other
  *                   two are tested against). */
 enum { AIM_FP64 = 0, AIM_MIXED = 1, AIM_FP64_NATIVE = 2 };

@@ -1,6 +1,6 @@
 // Double-float complex arithmetic: FP64-class accuracy on the FP32 pipe.
 //
-// GB300's FP64 rate is about 1/58 of its FP32 rate, so the FP64-accurate grid product runs its
+// GB300's FP64 rate is about 1/64 of its FP32 rate, so the FP64-accurate grid product runs its
 // FFTs in "double-float" arithmetic: every real value is an unevaluated sum hi + lo of two
 // floats (T. J. Dekker, "A floating-point technique for extending the available precision",
 // 1971); inputs are split with |lo| <= ulp(hi)/2, results are left unnormalised (see df_add). Sums use Knuth's error-free TwoSum, products the FMA-based
