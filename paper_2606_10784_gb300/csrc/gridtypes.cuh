@@ -41,10 +41,6 @@ template <typename CT> __device__ __forceinline__ CT czero();
 template <> __device__ __forceinline__ float2 czero<float2>() { return float2{0.f, 0.f}; }
 template <> __device__ __forceinline__ double2 czero<double2>() { return double2{0.0, 0.0}; }
 template <> __device__ __forceinline__ dfc czero<dfc>() { return dfc{0.f, 0.f, 0.f, 0.f}; }
-// exact zero test (either sign of zero)
-__device__ __forceinline__ bool cis_zero(float2 v) { return v.x == 0.f && v.y == 0.f; }
-__device__ __forceinline__ bool cis_zero(double2 v) { return v.x == 0.0 && v.y == 0.0; }
-__device__ __forceinline__ bool cis_zero(dfc v) { return v.xh == 0.f && v.xl == 0.f && v.yh == 0.f && v.yl == 0.f; }
 
 template <typename CT> __device__ __forceinline__ CT cfrom(double re, double im);
 template <> __device__ __forceinline__ float2 cfrom<float2>(double re, double im) {

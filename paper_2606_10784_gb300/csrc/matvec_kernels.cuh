@@ -132,31 +132,19 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_fwd(Row
     }
   }
   __syncthreads();
-  // pass 0 (radix E, Ns = 1): the transform of a and/or of a w^n. A row holds only tens of
-  // active points, so most threads read E zeros here: they skip the products and the DFTs, whose
-  // result would be zeros (warps where every thread does save the issue slots)
+  // pass 0 (radix E, Ns = 1): the transform of a and/or of a w^n
   {
     const int lognb = a.logH - LOGE;
     T2 v[NF][1 << LOGE];
-    bool any = false;
 #pragma unroll
     for (int r = 0; r < (1 << LOGE); ++r) {
-      const T2 x = sm[fbA + padi<LOGE>(j + (r << lognb))];
-      any = any || !cis_zero(x);
+      const int nn = j + (r << lognb);
+      const T2 x = sm[fbA + padi<LOGE>(nn)];
 #pragma unroll
-      for (int f = 0; f < NF; ++f) v[f][r] = x;
+      for (int f = 0; f < NF; ++f) v[f][r] = (TPT == 1 ? half : f) ? cmul(x, ldro(&tw[nn])) : x;
     }
-    if (any) {
 #pragma unroll
-      for (int r = 0; r < (1 << LOGE); ++r) {
-        const int nn = j + (r << lognb);
-#pragma unroll
-        for (int f = 0; f < NF; ++f)
-          if (TPT == 1 ? half : f) v[f][r] = cmul(v[f][r], ldro(&tw[nn]));
-      }
-#pragma unroll
-      for (int f = 0; f < NF; ++f) dft_reg<(1 << LOGE), false>(v[f]);
-    }
+    for (int f = 0; f < NF; ++f) dft_reg<(1 << LOGE), false>(v[f]);
     __syncthreads();
 #pragma unroll
     for (int f = 0; f < NF; ++f)
