@@ -12,14 +12,16 @@
 //               (P/2+1)^2 values are stored), and the inverse DFT keeping rows < P/2 only:
 //               y[n] = IDFT_H(Y_even)[n] + w^-n IDFT_H(Y_odd)[n].
 //   k_row_inv   the inverse row DFT with the same split, scaled by 1/P^2, evaluated at the
-//               grid points the test projection reads (the restriction [.]_restr).
+//               grid points the test projection reads (the restriction [.]_restr): the two
+//               half-transforms are recombined only at those points.
 //   k_gather    y_i = sum over projections of coef * (P_t^T v)_i plus the near-field row
-//               (C x)_i, one warp per unknown, deterministic.
+//               (C x)_i, eight lanes per unknown, deterministic.
 // Each length-H transform runs as register-resident radix-E passes (fft_reg.cuh, E = 16 or 8
 // elements per thread, a schedule choice): the first
 // pass reads its operands straight from global memory (column and inverse row passes) and the
-// last pass writes straight to global memory, so shared memory carries only the exchanges
-// between passes. A thread owns TPT transforms: with TPT = 2 the even- and odd-half transforms
+// last pass writes straight to global memory (forward row and column passes; the inverse row
+// pass keeps its last pass in shared memory for the restriction), so shared memory carries only
+// the exchanges between passes. A thread owns TPT transforms: with TPT = 2 the even- and odd-half transforms
 // of a line sit in the same thread; with TPT = 1 they sit in adjacent lanes and recombine
 // through a lane shuffle (half the registers per thread, twice the threads). Which one is
 // faster depends on the element type; the autotuner measures both.
