@@ -559,7 +559,7 @@ aim_status aim_query_bytes(const aim_geometry* geometry, const aim_grid* grid, c
   const size_t chan = (size_t)(te ? 3 : 1) * nrhs;
   const size_t el = precision == AIM_MIXED ? 8 : 16;
   size_t b = 0;
-  b += 2 * (H + 1) * (H + 1) * (16 + 8);            // spectra (double + float)
+  b += 2 * (H + 1) * (H + 1) * (16 + 16 + 8);       // spectra (binary64, double-float, complex64)
   b += (H + 1) * (H + 1) * 16;                      // setup temporary (kernel samples)
   b += nodes * s * s * (4 + 8 * (te ? 4 : 1)) * 2;  // projections, both orders
   b += (size_t)n * 64 * (4 + 16 + 8) * (te ? 2 : 1);  // near field (bound 64 per row)
