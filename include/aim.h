@@ -38,6 +38,9 @@
  *     for the last failure on the calling thread is returned by aim_last_error().
  *   - Calls on one context must not overlap (no internal locking); different contexts may
  *     be used concurrently from different threads and streams.
+ *   - A context lives on the CUDA device that was current at aim_setup. Every call that
+ *     enqueues work on it returns AIM_EINVAL, before any launch, when another device is
+ *     current on the calling thread.
  */
 #ifndef AIM_GB300_H
 #define AIM_GB300_H
@@ -233,23 +236,26 @@ aim_status aim_grid_product(aim_ctx* ctx, int filtered, int nrhs, const void* u,
 #define AIM_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
 
 /* The grid product of aim_grid_product without any allocation. This entry point has no
- * counterpart in the paper; it exists for callers that cannot allocate device memory when they
- * need a product: code running while a CUDA graph is being captured (allocation calls cannot be
- * captured), real-time loops whose device memory is fixed before they start, and hosts that
- * forbid cudaMalloc after start-up. aim_grid_product may grow the context's workspace with
- * cudaMalloc the first time it sees a larger batch; this variant instead keeps its scratch (the
- * tiled intermediate grid) in a fixed array of AIM_NOALLOC_SCRATCH_BYTES compiled into the
- * library's device image. Every GPU that loads the library holds that array until the process
- * exits. The call makes no cudaMalloc, cudaFree or other allocating call.
- * Same result as aim_grid_product with the same arguments. u and v must be device pointers.
+ * counterpart in the paper. It is for callers that cannot allocate device memory at the moment
+ * they need a product: real-time loops whose device memory is fixed before they start (an
+ * allocation there can stall or fail), hosts that forbid cudaMalloc after start-up, and code
+ * running inside another runtime's memory pool that third-party libraries may not grow.
+ * aim_grid_product may grow the context's workspace with cudaMalloc the first time it sees a
+ * larger batch; this variant instead keeps its scratch (the tiled intermediate grid) in a fixed
+ * array of AIM_NOALLOC_SCRATCH_BYTES compiled into the library's device image. Every GPU that
+ * loads the library holds that array until the process exits. The call makes no cudaMalloc,
+ * cudaFree or other allocating call.
+ * Same result as aim_grid_product with the same arguments, bit for bit. u and v must be device
+ * pointers on the context's device, which must be current.
  * The first call on each device looks up the array's device address (cudaGetSymbolAddress,
  * once per device, under a lock); make that first call before any stream capture.
  * Every call shares the one array and leaves its contents there; nothing in it needs to start at
  * zero (each product writes all of the scratch it later reads). Calls that overlap on the GPU -
  * from any context, stream or thread - race on the array; the caller must serialise them.
  * Errors: AIM_EINVAL if the intermediate grid (nrhs * fft_P * active rows * 16 bytes, 8 in
- * AIM_MIXED) exceeds AIM_NOALLOC_SCRATCH_BYTES or u, v are not device memory; AIM_ESTATE while
- * kernel timing (aim_profile_start) is active, because timing creates events. */
+ * AIM_MIXED) exceeds AIM_NOALLOC_SCRATCH_BYTES, u or v is not device memory, or the current
+ * device is not the context's; AIM_ESTATE while kernel timing (aim_profile_start) is active,
+ * because timing creates events. */
 aim_status aim_grid_product_noalloc(aim_ctx* ctx, int filtered, int nrhs, const void* u, void* v,
                                     int precision, void* stream);
 
@@ -265,10 +271,23 @@ aim_status aim_solve(aim_ctx* ctx, aim_op system, int nrhs, const void* rhs, voi
                      int x0_given, const aim_solve_opts* opts, aim_solve_info* info,
                      void* stream);
 
-/* Upper bound on the device bytes aim_setup + aim_reserve(nrhs, precision) would hold,
- * without building anything (admission control). */
+/* Device bytes that aim_setup followed by aim_reserve(nrhs, precision) would hold at their
+ * peak, without touching the GPU (admission control; no counterpart in the paper). The count
+ * runs the host part of the setup (grid, projections of Eq. 7 and the near-field pattern for
+ * stencil->near_radius), so it is exact for the arrays, and takes every allocation in whole
+ * 2 MiB allocator pages, so it is an upper bound on what the device commits. It does not
+ * include a solve's Krylov basis (see aim_query_solve_bytes). Errors as for aim_setup's
+ * argument checks (AIM_EINVAL). */
 aim_status aim_query_bytes(const aim_geometry* geometry, const aim_grid* grid,
                            const aim_stencil* stencil, int nrhs, int precision, size_t* bytes);
+
+/* Upper bound, like aim_query_bytes, on the device bytes a context holds after aim_setup and
+ * aim_solve(nrhs, opts): the FP64 grid workspaces every solve reserves, the staging buffers, the
+ * Krylov basis and reduction buffers for opts->restart, and the refinement vectors of a mixed
+ * solve. Only opts->restart and opts->precision are read. */
+aim_status aim_query_solve_bytes(const aim_geometry* geometry, const aim_grid* grid,
+                                 const aim_stencil* stencil, int nrhs, const aim_solve_opts* opts,
+                                 size_t* bytes);
 
 /* Launch accounting and kernel timing (no counterpart in the paper; for measurement).
  * aim_launch_count: kernels the library has enqueued in this process so far (all contexts).

@@ -35,7 +35,8 @@ filtered kernel obtained by an explicit DFT matrix. Tests check one against the 
 
 Pins: Lagrange exactness on polynomials; direct sum == FFT product; filter idempotence
 and identity for alpha above the grid Nyquist radius; unfiltered AIM -> dense exact
-operator as m and s grow; filtered spectrum on a circle against the closed form.
+operator as m and s grow, for TE (S, N) and TM (Z, on a circle and a star); the TM AIM
+solution against the cylinder series; filtered spectrum on a circle against the closed form.
 """
 from __future__ import annotations
 

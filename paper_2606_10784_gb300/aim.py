@@ -126,6 +126,9 @@ def lib() -> ctypes.CDLL:
     L.aim_query_bytes.argtypes = [ctypes.POINTER(Geometry), ctypes.POINTER(Grid), ctypes.POINTER(Stencil), i, i,
                                   ctypes.POINTER(ctypes.c_size_t)]
     L.aim_query_bytes.restype = i
+    L.aim_query_solve_bytes.argtypes = [ctypes.POINTER(Geometry), ctypes.POINTER(Grid), ctypes.POINTER(Stencil), i,
+                                        ctypes.POINTER(SolveOpts), ctypes.POINTER(ctypes.c_size_t)]
+    L.aim_query_solve_bytes.restype = i
     L.aim_grid_product_noalloc.argtypes = [vp, i, i, vp, vp, i, vp]
     L.aim_grid_product_noalloc.restype = i
     L.aim_autotune.argtypes = [vp, i, i, vp, ctypes.POINTER(Schedule)]
@@ -189,11 +192,25 @@ def _geometry(nodes: np.ndarray, form: int, quad_p: int):
 
 
 def query_bytes(nodes, form: int, m: int, s: int = 4, quad_p: int = 4, fft_P: int = 0, nrhs: int = 1,
-                precision: int = FP64) -> int:
+                precision: int = FP64, near_radius: float = 0.0) -> int:
+    """Upper bound on the device bytes of aim_setup + aim_reserve(nrhs, precision)."""
     g, keep = _geometry(nodes, form, quad_p)
     out = ctypes.c_size_t(0)
-    _check(lib().aim_query_bytes(ctypes.byref(g), ctypes.byref(Grid(m, 0.0, fft_P)), ctypes.byref(Stencil(s, 0.0)),
-                                 nrhs, precision, ctypes.byref(out)), "aim_query_bytes")
+    _check(lib().aim_query_bytes(ctypes.byref(g), ctypes.byref(Grid(m, 0.0, fft_P)),
+                                 ctypes.byref(Stencil(s, float(near_radius))), nrhs, precision, ctypes.byref(out)),
+           "aim_query_bytes")
+    return out.value
+
+
+def query_solve_bytes(nodes, form: int, m: int, s: int = 4, quad_p: int = 4, fft_P: int = 0, nrhs: int = 1,
+                      restart: int = 50, precision: int = FP64, near_radius: float = 0.0) -> int:
+    """Upper bound on the device bytes of a context after aim_setup + aim_solve(nrhs, restart, precision)."""
+    g, keep = _geometry(nodes, form, quad_p)
+    out = ctypes.c_size_t(0)
+    opts = SolveOpts(1e-8, int(restart), 1, int(precision), 0.0, 0)
+    _check(lib().aim_query_solve_bytes(ctypes.byref(g), ctypes.byref(Grid(m, 0.0, fft_P)),
+                                       ctypes.byref(Stencil(s, float(near_radius))), int(nrhs), ctypes.byref(opts),
+                                       ctypes.byref(out)), "aim_query_solve_bytes")
     return out.value
 
 

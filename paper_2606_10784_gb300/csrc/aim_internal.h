@@ -18,6 +18,12 @@ struct dfc;   // double-float complex (dfloat.cuh)
 // ------------------------------------------------------------------------------------
 void set_error(const std::string& msg);
 aim_status fail(aim_status st, const std::string& msg);
+}  // namespace aim
+struct aim_ctx;
+namespace aim {
+// AIM_EINVAL unless the calling thread's current CUDA device is the one the context was set up on
+// (every array of a context lives on that device)
+aim_status check_device(const aim_ctx* ctx);
 
 #define AIM_CUDA_TRY(expr)                                                              \
   do {                                                                                  \
@@ -236,9 +242,10 @@ aim_status device_rhs_planewave(aim_ctx* ctx, int nrhs, const double* angles_dev
 template <typename T>
 aim_status grid_pass(aim_ctx* ctx, const PassSpec& spec, int nrhs, const double2* x, double2* y,
                      cudaStream_t st);
+// the grid product on full m x m grids with an explicit intermediate buffer (inter, inter_bytes)
 template <typename T>
-aim_status grid_product_dense(aim_ctx* ctx, bool filtered, int nrhs, const double2* u, double2* v,
-                              cudaStream_t st);
+aim_status grid_product_dense(aim_ctx* ctx, bool filtered, int nrhs, const double2* u, double2* v, void* inter,
+                              size_t inter_bytes, cudaStream_t st);
 aim_status gram_inv_apply(aim_ctx* ctx, int nrhs, const double2* x, double2* y, cudaStream_t st);
 size_t inter_bytes_needed(const aim_ctx* ctx, int channels, int precision);
 
@@ -252,5 +259,8 @@ aim_status reserve(aim_ctx* ctx, int nrhs, int precision);
 // ------------------------------------------------------------------------------------
 aim_status gmres_solve(aim_ctx* ctx, aim_op system, int nrhs, const double2* b, double2* x,
                        const aim_solve_opts* opts, aim_solve_info* info, cudaStream_t st);
+// device bytes of the GMRES workspaces for n unknowns, nrhs vectors and a restart length
+size_t krylov_bytes(size_t n, int nrhs, int restart);
+size_t reduction_bytes(int nrhs, int restart);
 
 }  // namespace aim

@@ -49,6 +49,19 @@ static bool device_pointer(const void* p) {
   return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
 }
 
+aim_status check_device(const aim_ctx* ctx) {
+  int dev = -1;
+  const cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(AIM_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  }
+  if (dev != ctx->device)
+    return fail(AIM_EINVAL, "the current CUDA device (" + std::to_string(dev) + ") is not the context's device (" +
+                                std::to_string(ctx->device) + "); make it current before the call");
+  return AIM_OK;
+}
+
 static aim_status grow(void** buf, size_t* have, size_t need) {
   if (*have >= need) return AIM_OK;
   if (*buf) cudaFree(*buf);
@@ -244,21 +257,9 @@ static aim_status validate(const aim_geometry* g, double k, const aim_grid* grid
   return AIM_OK;
 }
 
-aim_status aim_setup(const aim_geometry* geometry, double k, const aim_grid* grid, const aim_stencil* stencil,
-                     const aim_filter* filter, void* stream, aim_ctx** out) {
-  if (!out) return fail(AIM_EINVAL, "out is null");
-  *out = nullptr;
-  AIM_TRY(validate(geometry, k, grid, stencil, filter));
-  const auto t0 = std::chrono::steady_clock::now();
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  aim_ctx* ctx = new (std::nothrow) aim_ctx();
-  if (!ctx) return fail(AIM_ENOMEM, "context allocation");
-  struct Guard {
-    aim_ctx* c;
-    ~Guard() { if (c) aim_destroy(c); }
-  } guard{ctx};
-
-  cudaGetDevice(&ctx->device);
+// The sizes and grid parameters of a context from the caller's description (no device work).
+static aim_status derive_params(aim_ctx* ctx, const aim_geometry* geometry, double k, const aim_grid* grid,
+                                const aim_stencil* stencil, const aim_filter* filter) {
   ctx->form = geometry->form;
   ctx->n = geometry->n_seg;
   ctx->m = grid->m;
@@ -282,6 +283,25 @@ aim_status aim_setup(const aim_geometry* geometry, double k, const aim_grid* gri
   ctx->near_radius = stencil->near_radius > 0.0 ? stencil->near_radius : ctx->s * ctx->eps;
   ctx->filter_enabled = filter && filter->enabled;
   ctx->alpha = ctx->filter_enabled ? filter->alpha : 0.0;
+  return AIM_OK;
+}
+
+aim_status aim_setup(const aim_geometry* geometry, double k, const aim_grid* grid, const aim_stencil* stencil,
+                     const aim_filter* filter, void* stream, aim_ctx** out) {
+  if (!out) return fail(AIM_EINVAL, "out is null");
+  *out = nullptr;
+  AIM_TRY(validate(geometry, k, grid, stencil, filter));
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  aim_ctx* ctx = new (std::nothrow) aim_ctx();
+  if (!ctx) return fail(AIM_ENOMEM, "context allocation");
+  struct Guard {
+    aim_ctx* c;
+    ~Guard() { if (c) aim_destroy(c); }
+  } guard{ctx};
+
+  cudaGetDevice(&ctx->device);
+  AIM_TRY(derive_params(ctx, geometry, k, grid, stencil, filter));
 
   HostSetup hs;
   AIM_TRY(host_setup(ctx, &hs));
@@ -305,6 +325,7 @@ aim_status aim_setup(const aim_geometry* geometry, double k, const aim_grid* gri
     AIM_TRY(upload(ctx, &ctx->prj.sc_w[q], hs.sc_w[q], st));
     AIM_TRY(upload(ctx, &ctx->prj.ga_w[q], hs.ga_w[q], st));
   }
+  const int P = ctx->P;
   std::vector<double2> tw(P);
   std::vector<float2> twf(P);
   for (int t = 0; t < P; ++t) {
@@ -356,6 +377,7 @@ aim_status aim_get_info(const aim_ctx* ctx, aim_info* info) {
 aim_status aim_reserve(aim_ctx* ctx, int nrhs, int precision) {
   if (!ctx) return fail(AIM_EINVAL, "null context");
   if (precision < AIM_FP64 || precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "precision must be 0, 1 or 2");
+  AIM_TRY(check_device(ctx));
   return reserve(ctx, nrhs, precision);
 }
 
@@ -381,6 +403,7 @@ aim_status aim_get_schedule(const aim_ctx* ctx, int precision, aim_schedule* sch
 aim_status aim_autotune(aim_ctx* ctx, int nrhs, int precision, void* stream, aim_schedule* chosen) {
   if (!ctx || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
   if (precision < AIM_FP64 || precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "precision must be 0, 1 or 2");
+  AIM_TRY(check_device(ctx));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   AIM_TRY(reserve(ctx, nrhs, precision));
   const size_t bytes = (size_t)ctx->n * nrhs * sizeof(double2);
@@ -430,6 +453,7 @@ aim_status aim_autotune(aim_ctx* ctx, int nrhs, int precision, void* stream, aim
 
 aim_status aim_rhs_planewave(aim_ctx* ctx, int nrhs, const double* angles, void* rhs, void* stream) {
   if (!ctx || !angles || !rhs || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
+  AIM_TRY(check_device(ctx));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)ctx->n * nrhs * sizeof(double2);
   AIM_TRY(stage(ctx, std::max(bytes, nrhs * sizeof(double)), bytes));
@@ -452,6 +476,7 @@ aim_status aim_matvec(aim_ctx* ctx, aim_op op, int nrhs, const void* x, void* y,
   if (!ctx || !x || !y || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
   if (precision < AIM_FP64 || precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "precision must be 0, 1 or 2");
   if (x == y) return fail(AIM_EINVAL, "x and y must not overlap");
+  AIM_TRY(check_device(ctx));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)ctx->n * nrhs * sizeof(double2);
   const bool dx = device_pointer(x), dy = device_pointer(y);
@@ -473,6 +498,7 @@ aim_status aim_matvec(aim_ctx* ctx, aim_op op, int nrhs, const void* x, void* y,
 aim_status aim_grid_product(aim_ctx* ctx, int filtered, int nrhs, const void* u, void* v, int precision, void* stream) {
   if (!ctx || !u || !v || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
   if (precision < AIM_FP64 || precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "precision must be 0, 1 or 2");
+  AIM_TRY(check_device(ctx));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)ctx->m * ctx->m * nrhs * sizeof(double2);
   const bool du = device_pointer(u), dv = device_pointer(v);
@@ -486,9 +512,11 @@ aim_status aim_grid_product(aim_ctx* ctx, int filtered, int nrhs, const void* u,
     uin = ctx->stage_in;
   }
   double2* vout = dv ? static_cast<double2*>(v) : ctx->stage_out;
-  if (precision == AIM_MIXED) AIM_TRY(grid_product_dense<float2>(ctx, filtered != 0, nrhs, uin, vout, st));
-  else if (precision == AIM_FP64_NATIVE) AIM_TRY(grid_product_dense<double2>(ctx, filtered != 0, nrhs, uin, vout, st));
-  else AIM_TRY(grid_product_dense<dfc>(ctx, filtered != 0, nrhs, uin, vout, st));
+  void* in = ctx->inter;
+  const size_t ib = ctx->inter_bytes;
+  if (precision == AIM_MIXED) AIM_TRY(grid_product_dense<float2>(ctx, filtered != 0, nrhs, uin, vout, in, ib, st));
+  else if (precision == AIM_FP64_NATIVE) AIM_TRY(grid_product_dense<double2>(ctx, filtered != 0, nrhs, uin, vout, in, ib, st));
+  else AIM_TRY(grid_product_dense<dfc>(ctx, filtered != 0, nrhs, uin, vout, in, ib, st));
   if (!dv) {
     AIM_CUDA_TRY(cudaMemcpyAsync(v, vout, bytes, cudaMemcpyDeviceToHost, st));
     AIM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -510,6 +538,7 @@ aim_status aim_solve(aim_ctx* ctx, aim_op system, int nrhs, const void* rhs, voi
   if (!te && calderon)
     return fail(AIM_ESTATE, "Calderon systems need a TE context");
   if (te && system == AIM_OP_EFIE_ALPHA) return fail(AIM_ESTATE, "filtered EFIE system is TM only");
+  AIM_TRY(check_device(ctx));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)ctx->n * nrhs * sizeof(double2);
   const bool dr = device_pointer(rhs), dx = device_pointer(x);
@@ -542,30 +571,79 @@ aim_status aim_solve(aim_ctx* ctx, aim_op system, int nrhs, const void* rhs, voi
   return s;
 }
 
-aim_status aim_query_bytes(const aim_geometry* geometry, const aim_grid* grid, const aim_stencil* stencil, int nrhs,
-                           int precision, size_t* bytes) {
+// Device bytes of one cudaMalloc of `b` bytes as the allocator commits them (2 MiB pages).
+static size_t committed(size_t b) {
+  constexpr size_t kPage = (size_t)2 << 20;
+  return b == 0 ? 0 : (b + kPage - 1) / kPage * kPage;
+}
+
+// Exact sizes of what aim_setup and aim_reserve(nrhs, precision) allocate, from the host-side
+// setup (active grid points, projection lists, near-field pattern, Gram band), each allocation
+// counted in whole allocator pages, plus the largest set of setup temporaries alive at once.
+static aim_status query_context_bytes(const aim_geometry* geometry, const aim_grid* grid, const aim_stencil* stencil,
+                                      int nrhs, int precision, size_t* bytes) {
   if (!geometry || !grid || !stencil || !bytes || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
-  const int n = geometry->n_seg, m = grid->m, s = stencil->s, p = geometry->quad_p;
-  int P = grid->fft_P;
-  if (P == 0) {
-    P = kMinP;
-    while (P < 2 * m - 1) P *= 2;
+  if (precision < AIM_FP64 || precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "precision must be 0, 1 or 2");
+  // k and the filter do not change any size: validate with placeholders
+  AIM_TRY(validate(geometry, 1.0, grid, stencil, nullptr));
+  aim_ctx tmp;
+  AIM_TRY(derive_params(&tmp, geometry, 1.0, grid, stencil, nullptr));
+  HostSetup hs;
+  AIM_TRY(host_setup(&tmp, &hs));
+  const bool te = tmp.form == AIM_TE_P1_GALERKIN;
+  const size_t n = tmp.n, m = tmp.m, P = tmp.P, H = tmp.H, nact = hs.n_act;
+  const size_t nrows = (size_t)(hs.row_hi - hs.row_lo + 1);
+  const size_t nsc = hs.sc_col.size(), nga = hs.ga_act.size();
+  const size_t nnz = hs.near_col.size(), nq = (H + 1) * (H + 1);
+  size_t b = 0;
+  // persistent arrays of the context
+  b += committed(n * 16);                                        // vertices
+  b += committed((m + 1) * 4) + committed(nact * 4);             // row_ptr, act_ix
+  b += committed((nact + 1) * 4) + committed(nsc * 4);           // scatter CSR
+  b += committed((n + 1) * 4) + committed(nga * 4);              // gather CSR
+  b += hs.nproj * (committed(nsc * 8) + committed(nga * 8));     // projection weights
+  b += committed(P * 16) + committed(P * 8) + committed(P * 16); // twiddles
+  b += committed(hs.gram_inv.size() * 8);
+  const size_t nvals = te ? 2 : 1;
+  if (nnz > 0) b += committed((n + 1) * 4) + committed(nnz * 4) + nvals * (committed(nnz * 16) + committed(nnz * 8));
+  b += 2 * (committed(nq * 16) + committed(nq * 8) + committed(nq * 16)) + committed((H + 1) * 4);   // spectra
+  // setup temporaries (freed before aim_setup returns)
+  size_t t = committed(nq * 16);                                 // kernel samples
+  if (nnz > 0) {
+    t += committed(nact * 4);
+    if (te) {
+      const size_t npairs = hs.seg_e.size();
+      t += 2 * committed(npairs * 4) + committed(nnz * 4 * 4) + committed(npairs * 4 * 16);
+    } else {
+      t += committed((n + 1) * 4) + committed(hs.sr_act.size() * 4) + committed(hs.sr_w.size() * 8);
+    }
   }
-  const size_t H = P / 2;
-  const bool te = geometry->form == AIM_TE_P1_GALERKIN;
-  // active points bounded by all stencil points; rows bounded by m
-  const size_t nodes = (size_t)n * p * (te ? 2 : 1) + (te ? 0 : n);
-  const size_t nact = std::min((size_t)m * m, nodes * s * s);
+  b += t;
+  // grid workspaces of aim_reserve(nrhs, precision)
   const size_t chan = (size_t)(te ? 3 : 1) * nrhs;
   const size_t el = precision == AIM_MIXED ? 8 : 16;
+  b += committed(chan * P * nrows * el) + committed(chan * nact * el) + committed(2 * (size_t)nrhs * n * 16);
+  *bytes = b;
+  return AIM_OK;
+}
+
+aim_status aim_query_bytes(const aim_geometry* geometry, const aim_grid* grid, const aim_stencil* stencil, int nrhs,
+                           int precision, size_t* bytes) {
+  return query_context_bytes(geometry, grid, stencil, nrhs, precision, bytes);
+}
+
+aim_status aim_query_solve_bytes(const aim_geometry* geometry, const aim_grid* grid, const aim_stencil* stencil,
+                                 int nrhs, const aim_solve_opts* opts, size_t* bytes) {
+  if (!opts || !bytes || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
+  if (opts->restart < 1 || opts->restart > 10000) return fail(AIM_EINVAL, "restart must be in 1..10000");
+  if (opts->precision < AIM_FP64 || opts->precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "bad precision");
+  // every solve reserves the FP64 grid workspaces (the largest), the mixed one as well
   size_t b = 0;
-  b += 2 * (H + 1) * (H + 1) * (16 + 16 + 8);       // spectra (binary64, double-float, complex64)
-  b += (H + 1) * (H + 1) * 16;                      // setup temporary (kernel samples)
-  b += nodes * s * s * (4 + 8 * (te ? 4 : 1)) * 2;  // projections, both orders
-  b += (size_t)n * 64 * (4 + 16 + 8) * (te ? 2 : 1);  // near field (bound 64 per row)
-  b += (size_t)n * (2 * kGramBand + 1 + kGramDenseMax) * 8;
-  b += chan * P * m * el + chan * nact * el;        // grid workspaces
-  b += (size_t)(2 + 2 + 54) * n * nrhs * 16;        // vectors, staging, Krylov (restart 50)
+  AIM_TRY(query_context_bytes(geometry, grid, stencil, nrhs, AIM_FP64, &b));
+  const size_t n = geometry->n_seg;
+  b += 2 * committed(n * nrhs * 16);                                  // staging of b and x
+  b += committed(krylov_bytes(n, nrhs, opts->restart)) + committed(reduction_bytes(nrhs, opts->restart));
+  if (opts->precision == AIM_MIXED) b += committed(2 * n * nrhs * 16);   // residual and correction
   *bytes = b;
   return AIM_OK;
 }

@@ -573,7 +573,7 @@ static bool feasible_for(const Schedule& s, int logH, int logP) {
 
 template <typename CT, int TPT, int LOGE>
 static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdArgs fa, RowInvArgs ia,
-                             const Schedule& sc, cudaStream_t st) {
+                             void* inter, const Schedule& sc, cudaStream_t st) {
   const int min_row_threads = sc.min_row_threads;
   using T2 = CT;
   constexpr int LPT = 3 - TPT;
@@ -596,7 +596,7 @@ static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdAr
   fa.logP = ctx->logP;
   fa.row_lo = ctx->row_lo;
   fa.nrows = ctx->nrows;
-  fa.inter = ctx->inter;
+  fa.inter = inter;
   fa.rows_per_cta = rpc;
   AIM_TRY(ensure_smem(k_row_fwd<CT, TPT, LOGE>, sm_row));
   {
@@ -610,7 +610,7 @@ static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdAr
   int log_cols = 0;
   while ((1 << log_cols) < cols) ++log_cols;
   ColArgs ca;
-  ca.inter = ctx->inter;
+  ca.inter = inter;
   ca.spec = spec;
   ca.live = filtered ? ctx->specA_live : nullptr;
   ca.tw = tw;
@@ -632,7 +632,7 @@ static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdAr
   AIM_CUDA_TRY(cudaGetLastError());
 
   // row inverse
-  ia.inter = ctx->inter;
+  ia.inter = inter;
   ia.tw = tw;
   ia.logH = ctx->logH;
   ia.logP = ctx->logP;
@@ -651,21 +651,21 @@ static aim_status launch_tpt(aim_ctx* ctx, int channels, bool filtered, RowFwdAr
 
 template <typename CT>
 static aim_status launch_three_passes(aim_ctx* ctx, int channels, bool filtered, RowFwdArgs fa, RowInvArgs ia,
-                                      cudaStream_t st) {
+                                      void* inter, cudaStream_t st) {
   if (channels > 65535) return fail(AIM_EINVAL, "too many channels in one grid pass");
   if (ctx->H < 32) return fail(AIM_EINVAL, "embedding side P must be >= 64");
   const int p = precision_of((CT*)nullptr);
   const Schedule sc = ctx->sched[p];
   if (!feasible_for<CT>(sc, ctx->logH, ctx->logP)) return fail(AIM_EINVAL, "launch schedule not feasible");
   if constexpr (std::is_same<CT, double2>::value) {
-    return launch_tpt<CT, 2, 4>(ctx, channels, filtered, fa, ia, sc, st);
+    return launch_tpt<CT, 2, 4>(ctx, channels, filtered, fa, ia, inter, sc, st);
   } else {
     if (loge_of(sc) == 3) {
-      if (sc.tpt == 1) return launch_tpt<CT, 1, 3>(ctx, channels, filtered, fa, ia, sc, st);
-      return launch_tpt<CT, 2, 3>(ctx, channels, filtered, fa, ia, sc, st);
+      if (sc.tpt == 1) return launch_tpt<CT, 1, 3>(ctx, channels, filtered, fa, ia, inter, sc, st);
+      return launch_tpt<CT, 2, 3>(ctx, channels, filtered, fa, ia, inter, sc, st);
     }
-    if (sc.tpt == 1) return launch_tpt<CT, 1, 4>(ctx, channels, filtered, fa, ia, sc, st);
-    return launch_tpt<CT, 2, 4>(ctx, channels, filtered, fa, ia, sc, st);
+    if (sc.tpt == 1) return launch_tpt<CT, 1, 4>(ctx, channels, filtered, fa, ia, inter, sc, st);
+    return launch_tpt<CT, 2, 4>(ctx, channels, filtered, fa, ia, inter, sc, st);
   }
 }
 
@@ -697,7 +697,7 @@ aim_status grid_pass(aim_ctx* ctx, const PassSpec& spec, int nrhs, const double2
   ia.n_act = ctx->n_act;
   ia.row_ptr = ctx->row_ptr;
   ia.act_ix = ctx->act_ix;
-  AIM_TRY(launch_three_passes<CT>(ctx, channels, spec.filtered, fa, ia, st));
+  AIM_TRY(launch_three_passes<CT>(ctx, channels, spec.filtered, fa, ia, ctx->inter, st));
 
   GatherArgs ga{};
   ga.vact = ctx->vact;
@@ -737,10 +737,10 @@ aim_status grid_pass(aim_ctx* ctx, const PassSpec& spec, int nrhs, const double2
 }
 
 template <typename CT>
-aim_status grid_product_dense(aim_ctx* ctx, bool filtered, int nrhs, const double2* u, double2* v,
-                              cudaStream_t st) {
+aim_status grid_product_dense(aim_ctx* ctx, bool filtered, int nrhs, const double2* u, double2* v, void* inter,
+                              size_t inter_bytes, cudaStream_t st) {
   const int precision = precision_of((CT*)nullptr);
-  if (inter_bytes_needed(ctx, nrhs, precision) > ctx->inter_bytes)
+  if (inter == nullptr || inter_bytes_needed(ctx, nrhs, precision) > inter_bytes)
     return fail(AIM_ESTATE, "grid workspace not reserved for this many grids");
   AIM_CUDA_TRY(cudaMemsetAsync(v, 0, (size_t)nrhs * ctx->m * ctx->m * sizeof(double2), st));
   RowFwdArgs fa{};
@@ -754,7 +754,7 @@ aim_status grid_product_dense(aim_ctx* ctx, bool filtered, int nrhs, const doubl
   ia.dense_out = v;
   ia.m = ctx->m;
   ia.n_act = ctx->n_act;
-  return launch_three_passes<CT>(ctx, nrhs, filtered, fa, ia, st);
+  return launch_three_passes<CT>(ctx, nrhs, filtered, fa, ia, inter, st);
 }
 
 }  // namespace aim

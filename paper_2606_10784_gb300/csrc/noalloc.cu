@@ -1,12 +1,12 @@
 // Grid product with library-owned scratch: an entry point that allocates nothing.
 //
-// Some callers cannot allocate device memory at the moment they need a product: code that runs
-// while a CUDA graph is being captured (allocation calls are not capturable), real-time or
-// embedded loops whose device-memory footprint is fixed up front, and callers inside a memory
-// pool that does not allow growth. aim_grid_product may grow its workspace with cudaMalloc the
-// first time it sees a larger batch. This variant uses instead a fixed scratch array that lives
-// in the library's device image: every GPU that loads the library holds it until the process
-// exits, and every call shares it.
+// Some callers cannot allocate device memory at the moment they need a product: real-time or
+// embedded loops whose device-memory footprint is fixed before they start (an allocation there
+// can stall or fail unpredictably), hosts that forbid cudaMalloc after start-up, and code that
+// runs inside another runtime's memory pool that does not let third-party libraries grow it.
+// aim_grid_product may grow its workspace with cudaMalloc the first time it sees a larger batch.
+// This variant uses instead a fixed scratch array that lives in the library's device image:
+// every GPU that loads the library holds it until the process exits, and every call shares it.
 #include <mutex>
 
 #include "aim_internal.h"
@@ -20,15 +20,15 @@ bool profiling_active();
 static __device__ __align__(256) unsigned char g_noalloc_scratch[AIM_NOALLOC_SCRATCH_BYTES];
 
 namespace {
+constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mu;
-void* g_scratch_addr[64] = {};   // per device: the device address of g_noalloc_scratch
+void* g_scratch_addr[kMaxDevices] = {};   // per device: the device address of g_noalloc_scratch
 }  // namespace
 
-// Device address of the scratch array on the current device (set up once per device).
-static aim_status scratch_address(void** out) {
-  int dev = 0;
-  AIM_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) return fail(AIM_EINVAL, "device index out of range for the no-alloc scratch");
+// Device address of the scratch array on `dev`, which must be the current device (looked up once
+// per device; in host code the array's name is only a host-side stand-in, not a device address).
+static aim_status scratch_address(int dev, void** out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(AIM_EINVAL, "device index out of range for the no-alloc scratch");
   std::lock_guard<std::mutex> lk(g_scratch_mu);
   if (g_scratch_addr[dev] == nullptr) {
     void* p = nullptr;
@@ -51,6 +51,8 @@ extern "C" aim_status aim_grid_product_noalloc(aim_ctx* ctx, int filtered, int n
                                                int precision, void* stream) {
   if (!ctx || !u || !v || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
   if (precision < AIM_FP64 || precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "precision must be 0, 1 or 2");
+  // the scratch address is per device, and the context's spectra and twiddles live on ctx->device
+  AIM_TRY(check_device(ctx));
   if (profiling_active())
     return fail(AIM_ESTATE, "kernel timing (aim_profile_start) creates events; stop it before the no-alloc call");
   const size_t need = inter_bytes_needed(ctx, nrhs, precision);
@@ -67,20 +69,15 @@ extern "C" aim_status aim_grid_product_noalloc(aim_ctx* ctx, int filtered, int n
       (av.type != cudaMemoryTypeDevice && av.type != cudaMemoryTypeManaged))
     return fail(AIM_EINVAL, "u and v must be device pointers");
   void* scratch = nullptr;
-  AIM_TRY(scratch_address(&scratch));
-  // run the product with the scratch array standing in for the context's workspace
-  void* saved = ctx->inter;
-  const size_t saved_bytes = ctx->inter_bytes;
-  ctx->inter = scratch;
-  ctx->inter_bytes = (size_t)AIM_NOALLOC_SCRATCH_BYTES;
+  AIM_TRY(scratch_address(ctx->device, &scratch));
+  // the scratch goes to the product as its intermediate buffer; the context's own workspace is
+  // neither used nor touched
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  aim_status s;
   const double2* uin = static_cast<const double2*>(u);
   double2* vout = static_cast<double2*>(v);
-  if (precision == AIM_MIXED) s = grid_product_dense<float2>(ctx, filtered != 0, nrhs, uin, vout, st);
-  else if (precision == AIM_FP64_NATIVE) s = grid_product_dense<double2>(ctx, filtered != 0, nrhs, uin, vout, st);
-  else s = grid_product_dense<dfc>(ctx, filtered != 0, nrhs, uin, vout, st);
-  ctx->inter = saved;
-  ctx->inter_bytes = saved_bytes;
-  return s;
+  const size_t sb = (size_t)AIM_NOALLOC_SCRATCH_BYTES;
+  if (precision == AIM_MIXED) return grid_product_dense<float2>(ctx, filtered != 0, nrhs, uin, vout, scratch, sb, st);
+  if (precision == AIM_FP64_NATIVE)
+    return grid_product_dense<double2>(ctx, filtered != 0, nrhs, uin, vout, scratch, sb, st);
+  return grid_product_dense<dfc>(ctx, filtered != 0, nrhs, uin, vout, scratch, sb, st);
 }

@@ -380,15 +380,23 @@ static void vcombine_df(const dfc* V, const dfc* c, int J, int n, int nrhs, doub
   k_vcombine_finish_df<<<(n * nrhs + 255) / 256, 256, 0, st>>>(part_df, nch, n, nrhs, sign, out, out_df);
 }
 
-static aim_status ensure_krylov(aim_ctx* ctx, int nrhs, int restart) {
+size_t krylov_bytes(size_t n, int nrhs, int restart) {
   // partial sums of the basis updates (chunks of kCgsChunk vectors) or of the inner products
   // (chunks of kDotChunk elements), whichever needs more
-  const size_t n = (size_t)ctx->n;
   const size_t nz = (n + kDotChunk - 1) / kDotChunk;
   const size_t part_vecs = std::max((size_t)(restart + kCgsChunk) / kCgsChunk, (nz * (restart + 1) + n - 1) / n);
   // basis (restart + 1, double-float), w, r, the current vector, w in double-float, partial sums
   const size_t nvec = (size_t)(restart + 1) + 4 + part_vecs;
-  const size_t need = nvec * nrhs * ctx->n * sizeof(double2);
+  return nvec * nrhs * n * sizeof(double2);
+}
+
+size_t reduction_bytes(int nrhs, int restart) {
+  // dots, dots2, norms, their double-float copies, and the active flags
+  return ((size_t)(restart + 2) * 5 + 1) * nrhs * sizeof(double2) + nrhs * sizeof(int);
+}
+
+static aim_status ensure_krylov(aim_ctx* ctx, int nrhs, int restart) {
+  const size_t need = krylov_bytes((size_t)ctx->n, nrhs, restart);
   if (ctx->kry_bytes < need) {
     if (ctx->kry) cudaFree(ctx->kry);
     ctx->kry = nullptr;
@@ -398,8 +406,7 @@ static aim_status ensure_krylov(aim_ctx* ctx, int nrhs, int restart) {
     ctx->kry = static_cast<double2*>(p);
     ctx->kry_bytes = need;
   }
-  // dots, dots2, norms, their double-float copies, and the active flags
-  const size_t rneed = ((size_t)(restart + 2) * 5 + 1) * nrhs * sizeof(double2) + nrhs * sizeof(int);
+  const size_t rneed = reduction_bytes(nrhs, restart);
   if (ctx->red_bytes < rneed) {
     if (ctx->red) cudaFree(ctx->red);
     if (ctx->red_host) cudaFreeHost(ctx->red_host);

@@ -2,7 +2,7 @@
 
 Requests (a contour, a wavenumber, grid and filter parameters, and 1..16 incidence angles)
 arrive over time. The server admits a request when a slot is free and the device-memory
-bound of its context (aim_query_bytes) fits in the remaining budget, runs it on that slot's
+bound of its context (aim_query_solve_bytes) fits in the remaining budget, runs it on that slot's
 own CUDA stream, and reports each request's latency from arrival to completion. Slots run
 concurrently, so the device work of requests admitted at different times overlaps.
 Contexts (kernel spectra, projections, near field, Krylov workspace) stay resident in an LRU
@@ -51,10 +51,10 @@ class SolveRequest:
 
 
 def request_bytes(req: SolveRequest) -> int:
-    """Device-memory bound of one request: its context (aim_query_bytes) plus its Krylov basis."""
-    krylov = (min(req.restart, req.max_iter) + 4) * len(req.angles) * len(req.nodes) * 16
-    return aim.query_bytes(req.nodes, aim.TE, req.m, s=req.s, quad_p=req.quad_p, fft_P=req.fft_P,
-                           nrhs=len(req.angles), precision=req.precision) + krylov
+    """Device-memory bound of one request: its context after the solve (aim_query_solve_bytes:
+    operators, grid workspaces, staging, Krylov basis for the request's restart length)."""
+    return aim.query_solve_bytes(req.nodes, aim.TE, req.m, s=req.s, quad_p=req.quad_p, fft_P=req.fft_P,
+                                 nrhs=len(req.angles), restart=req.restart, precision=req.precision)
 
 
 @dataclasses.dataclass

@@ -55,6 +55,41 @@ def test_query_bytes_is_host_only_and_scales(lib):
     assert 0 < b1 < b8 < big
 
 
+def test_query_bytes_counts_the_near_field_of_the_given_radius(lib):
+    # the count runs the host setup, so a near radius that takes in more pairs costs more bytes
+    # (the old bound assumed at most 64 entries per row whatever the radius)
+    from paper_2606_10784_gb300 import aim
+    nodes = synth.StarContour.from_seed(2).polygon(100.0, 1000)
+    base = aim.query_bytes(nodes, aim.TE, 256, nrhs=1)
+    wide = aim.query_bytes(nodes, aim.TE, 256, nrhs=1, near_radius=3.0)
+    # 3 wavelengths at 10 segments per wavelength: ~60 segments each side, ~120+ hats per row,
+    # two complex128 and two complex64 values plus a column per entry
+    assert wide - base > 1000 * 100 * (2 * 16 + 2 * 8 + 4) * 0.5
+
+
+def test_query_solve_bytes_adds_the_krylov_basis_of_the_restart(lib):
+    from paper_2606_10784_gb300 import aim
+    nodes = synth.circle_polygon(50.0, 3000)
+    b100 = aim.query_solve_bytes(nodes, aim.TE, 512, nrhs=4, restart=100)
+    b600 = aim.query_solve_bytes(nodes, aim.TE, 512, nrhs=4, restart=600)
+    basis = 500 * 4 * 3000 * 16          # 500 more basis vectors of n x nrhs complex128
+    assert basis <= b600 - b100 <= basis + (8 << 20)
+    assert b100 > aim.query_bytes(nodes, aim.TE, 512, nrhs=4)
+    mixed = aim.query_solve_bytes(nodes, aim.TE, 512, nrhs=4, restart=100, precision=aim.MIXED)
+    assert mixed >= b100
+
+
+def test_query_calls_reject_bad_arguments(lib):
+    from paper_2606_10784_gb300 import aim
+    nodes = synth.circle_polygon(1.0, 64)
+    with pytest.raises(aim.AimError) as exc:
+        aim.query_bytes(nodes, aim.TE, 4)
+    assert exc.value.status == aim.EINVAL
+    with pytest.raises(aim.AimError) as exc:
+        aim.query_solve_bytes(nodes, aim.TE, 32, restart=0)
+    assert exc.value.status == aim.EINVAL
+
+
 def test_setup_rejects_bad_arguments_before_touching_the_gpu(lib):
     from paper_2606_10784_gb300 import aim
     nodes = synth.circle_polygon(1.0, 64)

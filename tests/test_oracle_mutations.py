@@ -6,6 +6,7 @@ import math
 import numpy as np
 import pytest
 import scipy.fft
+import scipy.sparse as sp
 
 import synth
 from oracle import aim, dense, geometry, special
@@ -142,3 +143,61 @@ def test_planted_forward_transform_used_as_inverse(monkeypatch):
     brute = (T @ u.ravel()).reshape(m, m)
     monkeypatch.setattr(scipy.fft, "ifft2", lambda X, workers=None: scipy.fft.fft2(X) / (X.shape[-1] * X.shape[-2]))
     assert rel(aim.conv_fft(u, aim.dft2(c, direct=True)), brute) > 0.1
+
+
+# --------------------------------------------------------------------------------------
+# TM projections (pulse sources, midpoint collocation): each plant fails the TM pins
+# --------------------------------------------------------------------------------------
+def _tm_pin_fails():
+    from test_oracle_pins import _tm_aim_errors
+    return any(e48 >= 0.1 * e24 or e48 >= 3e-4 for e24, e48 in _tm_aim_errors())
+
+
+def test_planted_equal_pulse_weights(monkeypatch):
+    orig = aim.tm_projections
+
+    def bad(nodes, p, L, eps, m, s):
+        out = orig(nodes, p, L, eps, m, s)
+        nodes = np.asarray(nodes)
+        r, w, _ = geometry.gauss_nodes(nodes, p)
+        w = np.repeat(w.sum(axis=1, keepdims=True) / p, p, axis=1)   # Gauss weights replaced by h/p
+        ix0, iy0, W = aim.stencils(r, L, eps, s)
+        seg = np.arange(len(nodes))[:, None] * np.ones((1, p), dtype=np.int64)
+        rr, cc, dd = aim._coo_from_stencils(ix0, iy0, W, seg, w, m, s)
+        out["src"] = sp.csr_matrix((dd, (rr, cc)), shape=(m * m, len(nodes)))
+        return out
+    monkeypatch.setattr(aim, "tm_projections", bad)
+    assert _tm_pin_fails()
+
+
+def test_planted_collocation_at_vertex(monkeypatch):
+    orig = aim.tm_projections
+
+    def bad(nodes, p, L, eps, m, s):
+        out = orig(nodes, p, L, eps, m, s)
+        nodes = np.asarray(nodes)
+        jx0, jy0, V = aim.stencils(nodes, L, eps, s)                     # vertex instead of midpoint
+        rr, cc, dd = aim._coo_from_stencils(jx0, jy0, V, np.arange(len(nodes)), np.ones(len(nodes)), m, s)
+        out["tst"] = sp.csr_matrix((dd, (rr, cc)), shape=(m * m, len(nodes)))
+        return out
+    monkeypatch.setattr(aim, "tm_projections", bad)
+    assert _tm_pin_fails()
+
+
+def test_planted_swapped_source_and_test(monkeypatch):
+    orig = aim.tm_projections
+    monkeypatch.setattr(aim, "tm_projections",
+                        lambda *a: {"src": orig(*a)["tst"], "tst": orig(*a)["src"]})
+    assert _tm_pin_fails()
+
+
+def test_planted_shifted_segment_index(monkeypatch):
+    orig = aim.tm_projections
+
+    def bad(nodes, p, L, eps, m, s):
+        out = orig(nodes, p, L, eps, m, s)
+        src = out["src"].tocsc()
+        out["src"] = src[:, np.roll(np.arange(src.shape[1]), 1)].tocsr()
+        return out
+    monkeypatch.setattr(aim, "tm_projections", bad)
+    assert _tm_pin_fails()

@@ -254,6 +254,48 @@ def test_unfiltered_aim_converges_to_dense():
     assert errs[1][0] < 1e-3 and errs[1][1] < 1e-3
 
 
+def _tm_aim_errors():
+    """Relative error of the unfiltered TM AIM operator (pulse sources at p Gauss nodes, midpoint
+    collocation, near-field correction) against the dense exact Z, at m = 24 and 48."""
+    out = []
+    for nodes, seed in ((synth.circle_polygon(1.0, 128), 2), (synth.StarContour.from_seed(1).polygon(6.0, 120), 3)):
+        Z = dense.tm_dense(nodes, K)
+        x = synth.random_coeffs(len(nodes), 1, seed)[0]
+        out.append([rel(aim.TMOperators(nodes, K, m, 2 * m).Z(x), Z @ x) for m in (24, 48)])
+    return out
+
+
+def test_unfiltered_tm_aim_converges_to_dense():
+    # Sec. III-A on the TM system: the grid interpolation error of s = 4 Lagrange stencils falls
+    # like eps^4 (a factor 16 per halving of eps; measured 20), so a wrong pulse weight, a wrong
+    # collocation point, swapped source and test projections or a shifted segment index leave an
+    # error that does not vanish with m (the star breaks the symmetry a circle would hide)
+    for e24, e48 in _tm_aim_errors():
+        assert e48 < 0.1 * e24
+        assert e48 < 3e-4
+
+
+def test_tm_aim_converges_with_the_stencil_order():
+    nodes = synth.StarContour.from_seed(1).polygon(6.0, 120)
+    Z = dense.tm_dense(nodes, K)
+    x = synth.random_coeffs(120, 1, 3)[0]
+    e4 = rel(aim.TMOperators(nodes, K, 48, 96, s=4).Z(x), Z @ x)
+    e6 = rel(aim.TMOperators(nodes, K, 48, 96, s=6).Z(x), Z @ x)
+    assert e6 < 0.05 * e4 and e6 < 1e-5
+
+
+def test_tm_aim_solution_matches_series():
+    # the plain-method case: TM EFIE on the circle ka = 2 pi, N = 256 pulses, 64 x 64 grid, s = 4,
+    # GMRES to 1e-8; the closed-form current J_z = (2/(k eta pi a)) sum_n j^-n e^{jn phi}/H_n^(2)(ka)
+    N = 256
+    nodes = synth.circle_polygon(1.0, N)
+    op = aim.TMOperators(nodes, K, 64, 128, alpha=8 * K)
+    x, it, _ = solve.gmres(op.Z, dense.tm_rhs(nodes, K, 0.0), tol=1e-8, restart=100)
+    ref = special.tm_cylinder_current(2 * math.pi * (np.arange(N) + 0.5) / N, K, 1.0)
+    assert rel(x, ref) < 2e-3
+    assert it < 60
+
+
 def test_filter_is_identity_above_grid_nyquist():
     nodes = synth.StarContour.from_seed(6).polygon(4.0, 48)
     op = aim.TEOperators(nodes, K, 24, 48, near=False)
