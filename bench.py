@@ -4,16 +4,24 @@
 One step is one pass of the whole method for one scatterer: setup of every operator from the
 contour (quadrature, grid, projections, kernel spectrum and its circular truncation, near
 field, Gram inverse), the plane-wave excitation, and the GMRES solve of the filtered
-Calderon system G^-1 S^alpha G^-1 N j = G^-1 S^alpha G^-1 E to a relative residual of 1e-8.
+Calderon system G^-1 S^alpha G^-1 N j = G^-1 S^alpha G^-1 E to a relative residual of 1e-5.
 Workload: a seeded random smooth contour of perimeter 1000 wavelengths, 10 segments per
 wavelength (N = 10000), a 2048 x 2048 grid (P = 4096), 4 x 4 stencils, alpha = 2k, one
-right-hand side. Inputs are synthetic (no dataset exists for this workload).
+right-hand side, FP64 grid arithmetic (double-float). Inputs are synthetic (no dataset exists
+for this workload).
+
+The default line also carries the other parts of the metric as sub-results, each timed on its
+own: the same contour in mixed precision (complex64 grid, FP64 refinement to 1e-5), 64 plane
+waves in every launch on the perimeter-400 contour, and a served Poisson stream with p50/p99
+latency. The headline timed region runs the product path as shipped (no per-kernel events);
+the per-kernel table and the roofline come from one more step run under kernel timing.
 
 Under torchrun each rank solves its own contour (seed = rank): weak scaling, no collective in
 the data path; value = all ranks' solves / max-over-ranks time.
 
 --impl reference runs the CPU oracle (numpy/scipy FP64) on a bounded sample of the same
-workload on the host cores, rank 0 only.
+workload on the host cores, rank 0 only. --profile-case runs one operator of the single-solve
+workload for kernel profilers.
 """
 from __future__ import annotations
 
@@ -40,8 +48,20 @@ UNIT = "solves/s"
 SOLVE_TOL = 1e-5
 RESTART = 3000
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-FP64_PEAK_TFLOPS = 1.25   # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz (nominal GB300 FP64 rate)
 FALLBACK_HBM_GBS = 6800.0
+# FP32 pipe of GB300, the pipe double-float arithmetic runs on: 152 SMs x 128 FP32 lanes x 2 flop
+# (FMA) x 2.07 GHz (the maximum SM clock) = 80.5 TFLOP/s; derived from unit counts and clocks
+FP32_PIPE_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64 pipe: 152 SMs x 2 FP64 FMA units x 2 flop x 2.07 GHz (nominal, derived)
+FP64_PIPE_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+E2E_STEPS_MAX = 5
+
+# DRAM traffic of k_col_conv per launch (dram__bytes_read.sum + dram__bytes_write.sum), the mean of
+# the two launches of one filtered Calderon product (N: 3 channels, S^alpha: 1 channel), from one
+# ncu capture of the current kernel and default schedule at the single-solve size; the capture and
+# its command are in profiles/col_conv_*_single_solve_n10000.md. None where no capture of the
+# current kernel exists.
+COL_CONV_TRAFFIC = {"fp64": None, "mixed": None, "native": None}
 
 
 def parse():
@@ -54,14 +74,19 @@ def parse():
                     help="fp64: FP64-accurate double-float grid arithmetic; mixed: complex64 grid with FP64 "
                          "refinement; native: IEEE binary64 grid arithmetic")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sub", action="store_true", help="skip the mixed / batching / serving sub-results")
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--workload", choices=["single", "batching", "serving"], default="single",
-                    help="single: one filtered Calderon solve per step (the default line); batching: 64 "
-                         "right-hand sides per solve (perimeter 400 wl, 1024^2 grid); serving: a Poisson "
-                         "stream of requests with p50/p99 latency")
+                    help="single: one filtered Calderon solve per step (the default line, with sub-results); "
+                         "batching / serving: that sub-result alone as its own line")
     ap.add_argument("--requests", type=int, default=40, help="serving: timed requests (after 10%% warm-up)")
     ap.add_argument("--policy", choices=["sjf", "fifo"], default="sjf", help="serving: admission order")
     ap.add_argument("--nrhs", type=int, default=64, help="batching: right-hand sides per solve (angles 2 pi r/nrhs)")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="apply --op to a seeded vector of the single-solve workload --repeat times (for ncu)")
+    ap.add_argument("--op", default="N", help="profile case: operator")
+    ap.add_argument("--repeat", type=int, default=1, help="profile case: products")
+    ap.add_argument("--time", action="store_true", help="profile case: print mean ms per launch of each kernel")
     return ap.parse_args()
 
 
@@ -74,13 +99,13 @@ def workload_config(wl, precision, world):
                         "alpha=2k, 1 rhs, GMRES(%d) rel. residual %.0e" % (wl.n, wl.m, wl.m, wl.fft_P, RESTART, SOLVE_TOL),
             "N": wl.n, "grid_m": wl.m, "fft_P": wl.fft_P, "alpha_over_k": wl.alpha / wl.k, "nrhs": 1,
             "precision": precision, "contour_seed": "rank", "ranks": world,
-            "l2": "inputs larger than L2 (grid intermediate 3 x 2048 x 4096 complex per product > 129 MB)"}
+            "l2": "inputs larger than L2 (grid intermediate 3 x 1653 x 4096 complex per product > 129 MB)"}
 
 
 def load_peaks():
     try:
         with open(PEAKS_FILE) as f:
-            return json.load(f), "measured"
+            return json.load(f), "measured (MEASURED_PEAKS.json)"
     except Exception:
         return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
 
@@ -137,69 +162,69 @@ class ClockSampler:
                 "samples": len(sms)}
 
 
-# Flop costs of one complex operation in the kernels' own arithmetic (FMA = 2 flops).
-# Plain complex64/complex128: add 2, multiply 6. Double-float (each real an unevaluated sum of two
-# floats): an add is TwoSum (6) + 2 adds + FastTwoSum (3) = 11 per real part, so 22 per complex
-# add; a multiply's real part is two exact products (1 mul + 1 fma each = 6), TwoSum (6), 2 adds,
-# 4 cross-term fmas (8) and FastTwoSum (3) = 25, so 50 per complex multiply.
-CPLX_COST = {"plain": (2, 6), "df": (22, 50)}
-
-
-def fft_flops(logh: int, kind: str) -> float:
-    """Flops of one length-2^logh transform as the kernels run it: radix-16 passes (radix-2
-    decimation in frequency inside, 10 non-trivial rotations per 16-point DFT) plus one radix-2^r
-    pass; every pass but the first multiplies by R-1 twiddles, of which 11/4/1 (R = 16/8/4) are
-    formed as products of table powers."""
-    add, mul = CPLX_COST[kind]
-    h = 1 << logh
-
-    def dft(r):
-        lg = int(math.log2(r))
-        rot = {16: 10, 8: 2, 4: 0, 2: 0}[r]
-        return (r // 2) * lg * 2 * add + rot * mul
-
-    extra = {16: 11, 8: 4, 4: 1, 2: 0}
-    radices = [16] * (logh // 4) + ([1 << (logh % 4)] if logh % 4 else [])
-    total = 0.0
-    for p, r in enumerate(radices):
-        per = dft(r) + (0 if p == 0 else (r - 1 + extra[r]) * mul)
-        total += (h // r) * per
-    return total
-
-
-def col_conv_algorithmic(wl, info, precision, channels, filtered=False):
-    """Algorithmic work of one column-pass launch (the dominant kernel).
-
-    Bytes: each channel's m_rows x P intermediate read once and written once, plus the stored
-    (P/2+1)^2 spectrum read once per launch (all channels use the same spectrum). Flops: per column and channel four half-length
-    transforms (fft_flops), the w^n twiddle of the odd half, the spectral product of P points
-    and the recombination y = A + conj(w^n) B at every one of the H rows. For the filtered
-    spectrum only the columns that the mask keeps count (2 pi min(q, P - q) / (P eps) <= alpha):
-    the others need no transform, only a zero written per row.
-    """
+# --------------------------------------------------------------------------------------
+# roofline model of the dominant kernel (the column pass)
+# --------------------------------------------------------------------------------------
+def live_columns(wl, info, filtered):
+    """Columns of the P x P spectrum the column pass transforms, and the stored half-columns
+    (q' = 0..P/2) it reads. Filtered (Eq. 10): only columns with a bin inside the disc kappa <= alpha,
+    kappa(0, q) = 2 pi min(q, P - q)/(P eps); the others need no transform, only zeros."""
     P = wl.fft_P
     H = P // 2
-    rows = info["row_hi"] - info["row_lo"] + 1
-    kind = "df" if precision == "fp64" else "plain"
-    add, mul = CPLX_COST[kind]
-    b = 8 if precision == "mixed" else 16
     live_half = H + 1
     if filtered:
         live_half = sum(1 for q in range(H + 1) if 2.0 * math.pi * q / (P * info["eps"]) <= info["alpha"])
     live = sum(1 for q in range(P) if min(q, P - q) < live_half)
+    return live, live_half
+
+
+def col_conv_algorithmic(wl, info, precision, channels, filtered=False):
+    """Algorithmic bytes and flops of one column-pass launch.
+
+    Bytes (the pass model of the method): each channel's m_rows x P intermediate read once and
+    written once over the live columns (zeros written on the others), plus the stored
+    (P/2+1)^2 spectrum read once per launch (all channels share it); b = 8 bytes per complex in
+    mixed precision, 16 otherwise.
+    Flops (the method's own count, the FFT convention 5 L log2 L per length-L transform): per live
+    column and channel the pruned forward DFT of the m_rows nonzeros and the inverse DFT keeping
+    m_rows outputs, each as two length-H transforms (4 x 5 H log2 H), plus the spectral product
+    (6 flops per complex product at P points). The same count whatever the arithmetic.
+    """
+    P = wl.fft_P
+    H = P // 2
+    rows = info["row_hi"] - info["row_lo"] + 1
+    b = 8 if precision == "mixed" else 16
+    live, live_half = live_columns(wl, info, filtered)
     bytes_ = channels * (2 * rows * live * b + rows * (P - live) * b) + live_half * (H + 1) * b
-    per_col = 4 * fft_flops(int(math.log2(H)), kind) + H * mul + P * mul + H * (mul + add)
-    flops = channels * live * per_col
+    flops = channels * live * (4 * 5 * H * math.log2(H) + 6 * P)
     return bytes_, flops
 
 
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 152 SMs x 128 FP32 lanes x FMA x 2.07 GHz = 80.5
-
-# DRAM traffic of k_col_conv per launch (dram__bytes_read.sum + dram__bytes_write.sum), the mean of
-# the two launches of one filtered Calderon product (N: 3 channels, S^alpha: 1 channel), from one
-# ncu capture of the default schedule at the single-solve size; the profiles directory gives the
-# capture and its command. None where no capture matches the current kernel and schedule.
-COL_CONV_TRAFFIC = {"fp64": 531852928, "mixed": 202739328, "native": None}
+def roofline(prof, wl, info, precision, peaks, src, kernel_stream_note):
+    """Roofline of the column pass from one profiled step: achieved = algorithmic bytes per launch
+    / mean CUDA-event launch time (the Calderon product alternates the N launch, 3 channels, and
+    the S^alpha launch, 1 channel, so the per-launch model is the mean of the two)."""
+    name = next((k for k in prof if k.startswith("col_conv")), None)
+    if name is None:
+        return None
+    nl, tms = prof[name]
+    avg_s = tms / nl / 1e3
+    b3, f3 = col_conv_algorithmic(wl, info, precision, 3)
+    b1, f1 = col_conv_algorithmic(wl, info, precision, 1, filtered=True)
+    per_bytes = (b3 + b1) / 2
+    per_flops = (f3 + f1) / 2
+    ach = per_bytes / avg_s / 1e9
+    alu_peak = FP64_PIPE_TFLOPS if precision == "native" else FP32_PIPE_TFLOPS
+    return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "traffic": COL_CONV_TRAFFIC.get(precision),
+            "peak_source": src, "algorithmic_bytes_per_launch": per_bytes, "launches": nl,
+            "avg_launch_ms": avg_s * 1e3, "timing": kernel_stream_note,
+            "alu": {"method_flops_per_launch": per_flops, "achieved_tflops": per_flops / avg_s / 1e12,
+                    "pipe": "FP64" if precision == "native" else "FP32",
+                    "pipe_peak_tflops": alu_peak, "frac": per_flops / avg_s / 1e12 / alu_peak,
+                    "note": "the method's flops (5 L log2 L per transform, 6 per complex product) in the "
+                            "arithmetic of the mode; double-float runs each on ~8-20 FP32 instructions; pipe "
+                            "peak derived from 152 SMs x lanes x 2 flop x 2.07 GHz"}}
 
 
 def aggregate(elapsed: float, steps: int, world: int, device=None):
@@ -217,6 +242,61 @@ def aggregate(elapsed: float, steps: int, world: int, device=None):
     return elapsed, steps * world / elapsed
 
 
+def _kernel_table(prof):
+    return {k: {"launches": v[0], "total_ms": round(v[1], 3), "mean_ms": round(v[1] / max(v[0], 1), 5)}
+            for k, v in prof.items()}
+
+
+def _solve_once(aim, wl, prec, rhs, x, last=None):
+    ctx = aim.Context(wl.nodes, wl.k, aim.TE, wl.m, fft_P=wl.fft_P, alpha=wl.alpha)
+    ctx.rhs_planewave(wl.angles, rhs)
+    x.zero_()
+    info = ctx.solve("calderon_alpha", rhs, x, tol=SOLVE_TOL, restart=RESTART, max_iter=6000, precision=prec,
+                     inner_tol=0.0)
+    if last is not None:
+        last["info"] = info[0]
+        last["ctx_info"] = ctx.info()
+    ctx.close()
+
+
+def single_solve_line(aim, wl, precision, steps, warmup, world, rank, dev, barrier, with_profile=True):
+    """Times `steps` solves (setup + excitation + solve + destroy) after `warmup`, then one profiled
+    step for the per-kernel table and the roofline. Returns the pieces of the JSON line."""
+    import torch
+    prec = {"fp64": aim.FP64, "mixed": aim.MIXED, "native": aim.FP64_NATIVE}[precision]
+    rhs = torch.empty((1, wl.n), dtype=torch.complex128, device=dev)
+    x = torch.zeros_like(rhs)
+    last = {}
+    for _ in range(warmup):
+        _solve_once(aim, wl, prec, rhs, x, last)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev.index or 0)
+    sampler.start()
+    l0 = aim.launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        _solve_once(aim, wl, prec, rhs, x, last)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    elapsed = e0.elapsed_time(e1) / 1e3
+    launches = aim.launch_count() - l0
+    clocks = sampler.stop()
+    prof = None
+    if with_profile:
+        # one more step with every launch bracketed by CUDA events on its own stream
+        aim.profile_start()
+        _solve_once(aim, wl, prec, rhs, x)
+        torch.cuda.synchronize()
+        prof = aim.profile_stop()
+    return elapsed, launches, clocks, prof, last
+
+
 def gb300_arm(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -232,52 +312,20 @@ def gb300_arm(args):
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    prec = {"fp64": aim.FP64, "mixed": aim.MIXED, "native": aim.FP64_NATIVE}[args.precision]
     wl = workload(args.seed + rank)
-    rhs = torch.empty((1, wl.n), dtype=torch.complex128, device=dev)
-    x = torch.zeros_like(rhs)
-    last = {}
-
-    def step():
-        ctx = aim.Context(wl.nodes, wl.k, aim.TE, wl.m, fft_P=wl.fft_P, alpha=wl.alpha)
-        ctx.rhs_planewave(wl.angles, rhs)
-        x.zero_()
-        info = ctx.solve("calderon_alpha", rhs, x, tol=SOLVE_TOL, restart=RESTART, max_iter=6000, precision=prec,
-                         inner_tol=0.0)
-        last["info"] = info[0]
-        last["ctx_info"] = ctx.info()
-        ctx.close()
 
     def barrier():
         if world > 1:
             import torch.distributed as dist
             dist.barrier()
 
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    sampler = ClockSampler(local)
-    sampler.start()
-    aim.profile_start()
-    l0 = aim.launch_count()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        step()
-    e1.record()
-    torch.cuda.synchronize()
-    barrier()
-    torch.cuda.synchronize()
-    elapsed = e0.elapsed_time(e1) / 1e3
-    launches = aim.launch_count() - l0
-    prof = aim.profile_stop()
-    clocks = sampler.stop()
+    warm = max(3, args.warmup)
+    elapsed, launches, clocks, prof, last = single_solve_line(aim, wl, args.precision, args.steps, warm, world, rank,
+                                                              dev, barrier)
     elapsed, value = aggregate(elapsed, args.steps, world, dev)
 
     # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    prec = {"fp64": aim.FP64, "mixed": aim.MIXED, "native": aim.FP64_NATIVE}[args.precision]
     rhs_h = torch.empty((1, wl.n), dtype=torch.complex128, pin_memory=True)
     x_h = torch.empty((1, wl.n), dtype=torch.complex128, pin_memory=True)
     with aim.Context(wl.nodes, wl.k, aim.TE, wl.m, fft_P=wl.fft_P, alpha=wl.alpha) as c0:
@@ -289,109 +337,111 @@ def gb300_arm(args):
                   inner_tol=0.0)
         ctx.close()
 
+    e2e_steps = max(1, min(args.steps, E2E_STEPS_MAX))
     step_e2e()
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         step_e2e()
     torch.cuda.synchronize()
-    e2e_el, e2e_value = aggregate(time.perf_counter() - t0, args.steps, world, dev)
-    if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
-    e2e = {"value": e2e_value, "unit": UNIT,
+    e2e_el, e2e_value = aggregate(time.perf_counter() - t0, e2e_steps, world, dev)
+    e2e = {"value": e2e_value, "unit": UNIT, "steps": e2e_steps,
            "h2d_bytes_per_step": int(wl.nodes.nbytes + rhs_h.numel() * 16),
            "d2h_bytes_per_step": int(x_h.numel() * 16)}
 
+    subs = {}
+    if not args.no_sub and world == 1:
+        subs["mixed_precision"] = mixed_sub(aim, wl, dev)
+        subs["batching"] = batching_arm(args, aim, steps=1, warmup=1)
+        subs["serving"] = serving_arm(args, aim)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
     if rank != 0:
         return None
-    # roofline of the dominant kernel (largest total time in the timed region)
-    traffic = COL_CONV_TRAFFIC.get(args.precision)
     peaks, src = load_peaks()
-    top = max(prof.items(), key=lambda kv: kv[1][1])
-    name, (nl, tms) = top
-    avg_s = tms / nl / 1e3
     info = last["ctx_info"]
-    roof = None
-    if name.startswith("col_conv"):
-        # the Calderon product runs 3 channels (N) and 1 channel (S^alpha) per application
-        n_n = nl // 2
-        b3, f3 = col_conv_algorithmic(wl, info, args.precision, 3)
-        b1, f1 = col_conv_algorithmic(wl, info, args.precision, 1, filtered=True)
-        per_launch_bytes = (b3 + b1) / 2
-        per_launch_flops = (f3 + f1) / 2
-        if args.precision in ("fp64", "native"):
-            # FP64 mode runs double-float arithmetic on the FP32 pipe; native mode the FP64 pipe
-            peak = FP32_PEAK_TFLOPS if args.precision == "fp64" else FP64_PEAK_TFLOPS
-            ach = per_launch_flops / avg_s / 1e12
-            roof = {"bound": "alu", "kernel": name, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                    "frac": ach / peak, "traffic": traffic if name.startswith("col_conv") else None,
-                    "peak_source": ("FP32 pipe nominal: 152 SMs x 128 lanes x 2 flop x 2.07 GHz (derived; "
-                                    "MEASURED_PEAKS has no FP32 figure); flops counted in double-float arithmetic"
-                                    if args.precision == "fp64" else
-                                    "FP64 nominal: 152 SMs x 64 FP64 flop/clk x 2.07 GHz (derived)"),
-                    "algorithmic_flops_per_launch": per_launch_flops,
-                    "algorithmic_bytes_per_launch": per_launch_bytes,
-                    "hbm_frac_of_measured": per_launch_bytes / avg_s / 1e9 / peaks["hbm_gbs"],
-                    "launches": nl, "avg_launch_ms": avg_s * 1e3}
-        else:
-            ach = per_launch_bytes / avg_s / 1e9
-            roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "peak_source": src,
-                    "launches": nl, "avg_launch_ms": avg_s * 1e3}
-    kernels = {k: {"launches": v[0], "total_ms": round(v[1], 3)} for k, v in prof.items()}
+    roof = roofline(prof, wl, info, args.precision, peaks, src,
+                    "CUDA events on the launching stream, one profiled solve after the timed region")
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": max(3, args.warmup), "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "df64 (complex fp32-pair double-float grid and Gram-Schmidt products; c128 vectors)",
-                                                   "mixed": "c64 grid + f64 refinement",
-                                                   "native": "c128"}[args.precision],
+           "warmup": warm, "ms_per_step": elapsed / args.steps * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": {"fp64": "df64 (complex fp32-pair double-float grid and Gram-Schmidt products; c128 vectors)",
+                     "mixed": "c64 grid + f64 refinement", "native": "c128"}[args.precision],
            "data": "synthetic (seeded random smooth contour family)",
            "config": workload_config(wl, args.precision, world), "e2e": e2e, "gpu_launches": launches,
            "roofline": roof, "clocks": clocks, "solve": last["info"],
-           "setup_seconds_lib": last["ctx_info"]["setup_seconds"], "kernels": kernels}
+           "setup_seconds_lib": info["setup_seconds"], "kernels": _kernel_table(prof)}
+    out.update(subs)
     if not args.no_cpu_baseline and world == 1:
         out["cpu_baseline"] = cpu_baseline(wl, last["info"]["iters"])
     return out
 
 
+def mixed_sub(aim, wl, dev, steps=3):
+    """The same single-solve contour with the complex64 grid and FP64 refinement to 1e-5 (the
+    precision configuration), timed alone; its column pass is the kernel the HBM roofline is about."""
+    elapsed, launches, clocks, prof, last = single_solve_line(aim, wl, "mixed", steps, 1, 1, 0, dev, lambda: None)
+    peaks, src = load_peaks()
+    roof = roofline(prof, wl, last["ctx_info"], "mixed", peaks, src,
+                    "CUDA events on the launching stream, one profiled solve after the timed region")
+    return {"metric": "filtered Calderon solves/s at rel. residual 1e-5, complex64 grid + FP64 refinement",
+            "value": steps / elapsed, "unit": UNIT, "steps": steps, "warmup": 1,
+            "ms_per_step": elapsed / steps * 1e3, "gpu_launches": launches, "clocks": clocks,
+            "solve": last["info"], "roofline": roof, "kernels": _kernel_table(prof),
+            "config": "same contour and system as the headline; complex64 grid products and interpolation sums, "
+                      "FP64 near-field sums, Gram inverse, Arnoldi and outer residual"}
+
+
 # --------------------------------------------------------------------------------------
 # CPU oracle (baseline leg and reference arm)
 # --------------------------------------------------------------------------------------
-def oracle_sample(wl, iters, n_near_rows=64, n_matvec=1):
+def oracle_sample(wl, iters, iters_source, n_near_rows=64, n_matvec=3):
     """Times the oracle on a bounded sample of one solve and extrapolates to solves/s.
 
-    Sample: the oracle's grid kernel + spectrum (full size), projections (full size), the
-    near-field correction for `n_near_rows` rows scaled to N rows, and `n_matvec` filtered
-    Calderon products; solve time = setup + iters x product time, iters = the GPU solve's
-    GMRES iteration count.
+    Sample: the oracle's grid kernel + spectrum and projections (full size); the near-pair search
+    over the whole contour (full size, once); the exact near-field entries of `n_near_rows` rows,
+    whose cost per row is scaled to N rows; `n_matvec` filtered Calderon products (mean).
+    Solve time = setup + near field + iters x product time. The Arnoldi orthogonalisation of the
+    oracle's GMRES is not counted (it would add to the oracle's time).
     """
     from oracle import aim as oaim
     t0 = time.perf_counter()
     op = oaim.TEOperators(wl.nodes, wl.k, wl.m, wl.fft_P, alpha=wl.alpha, near=False, direct_dft=False)
     t_grid = time.perf_counter() - t0
-    rows = np.arange(0, wl.n, max(1, wl.n // n_near_rows))[:n_near_rows]
     t1 = time.perf_counter()
-    op._near_setup(rows=rows)
-    t_near = (time.perf_counter() - t1) * wl.n / len(rows)
-    x = synth.random_coeffs(wl.n, 1, 5)[0]
+    oaim.near_pairs_te(wl.nodes, op.near_radius)
+    t_pairs = time.perf_counter() - t1
+    rows = np.arange(0, wl.n, max(1, wl.n // n_near_rows))[:n_near_rows]
     t2 = time.perf_counter()
+    op._near_setup(rows=rows)               # its own pair search (t_pairs) + the entries of `rows`
+    t_rows = max(0.0, time.perf_counter() - t2 - t_pairs)
+    t_near = t_pairs + t_rows * wl.n / len(rows)
+    x = synth.random_coeffs(wl.n, 1, 5)[0]
+    op.calderon(x, filtered=True)           # first call factors G
+    t3 = time.perf_counter()
     for _ in range(n_matvec):
         op.calderon(x, filtered=True)
-    t_mv = (time.perf_counter() - t2) / n_matvec
+    t_mv = (time.perf_counter() - t3) / n_matvec
     solve_s = t_grid + t_near + iters * t_mv
     return {"value": 1.0 / solve_s, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "oracle setup (grid kernel, spectrum, projections) at full size + near field on %d of %d rows "
-                      "scaled + %d filtered Calderon product(s); solve = setup + %d x product" %
-                      (len(rows), wl.n, n_matvec, iters),
-            "seconds": {"grid_setup": t_grid, "near_field_scaled": t_near, "calderon_product": t_mv}}
+            "sample": "oracle setup (grid kernel, spectrum, projections) and near-pair search at full size; exact "
+                      "near entries of %d of %d rows, per-row cost scaled; mean of %d filtered Calderon products; "
+                      "solve = setup + near field + %d x product (%s)" %
+                      (len(rows), wl.n, n_matvec, iters, iters_source),
+            "seconds": {"grid_setup": t_grid, "near_pair_search": t_pairs, "near_entries_scaled": t_near - t_pairs,
+                        "calderon_product": t_mv}}
 
 
-GPU_ITERS_HINT = 1831  # GMRES iterations of the GPU solve of this workload (used by the reference arm)
+# GMRES iterations of the filtered Calderon solve of this contour to 1e-5 (the GPU solve's count,
+# FP64 mode; the oracle's GMRES on the same system takes the same count, which a GPU test checks on
+# reduced contours). The reference arm has no GPU run to read it from.
+SINGLE_SOLVE_ITERS = 1831
 
 
 def cpu_baseline(wl, iters):
-    return oracle_sample(wl, iters)
+    return oracle_sample(wl, iters, "iterations: the GPU solve's count in this run, the same system and tolerance")
 
 
 def reference_arm(args):
@@ -403,8 +453,8 @@ def reference_arm(args):
     times = []
     res = None
     for i in range(max(3, args.warmup) + args.steps):
-        t0 = time.perf_counter()
-        res = oracle_sample(wl, GPU_ITERS_HINT, n_near_rows=16, n_matvec=1)
+        res = oracle_sample(wl, SINGLE_SOLVE_ITERS, "iterations: %d, the GPU solve's count for this contour "
+                                                    "and tolerance" % SINGLE_SOLVE_ITERS, n_near_rows=16, n_matvec=1)
         if i >= max(3, args.warmup):
             times.append(1.0 / res["value"])
     value = len(times) / sum(times)
@@ -419,17 +469,21 @@ def reference_arm(args):
 
 
 # --------------------------------------------------------------------------------------
-# batching and serving workloads (separate JSON lines; the default line is "single")
+# batching and serving workloads (sub-results of the default line, or lines of their own)
 # --------------------------------------------------------------------------------------
-def batching_arm(args):
+def batching_arm(args, aim=None, steps=None, warmup=None):
     """nrhs plane waves (default 64, angles 2 pi r/nrhs) on one contour of perimeter 400 wl
     (N = 4000, 1024^2 grid), all right-hand sides in every grid launch, launch schedule from the
     autotuner. One step = setup + autotune + excitation + the batched filtered Calderon solve to 1e-5."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_2606_10784_gb300 import aim
-    prec = {"fp64": aim.FP64, "mixed": aim.MIXED, "native": aim.FP64_NATIVE}[args.precision]
+    if aim is None:
+        import __graft_entry__
+        __graft_entry__.build()
+        from paper_2606_10784_gb300 import aim
+    steps = args.steps if steps is None else steps
+    warmup = max(1, args.warmup) if warmup is None else warmup
+    precision = "mixed" if args.workload != "batching" else args.precision
+    prec = {"fp64": aim.FP64, "mixed": aim.MIXED, "native": aim.FP64_NATIVE}[precision]
     wl = synth.batching_scale(args.seed, nrhs=args.nrhs)
     R = len(wl.angles)
     rhs = torch.empty((R, wl.n), dtype=torch.complex128, device="cuda")
@@ -449,38 +503,41 @@ def batching_arm(args):
             ctx.matvec("calderon_alpha", rhs, x, precision=prec)
         ctx.close()
 
-    for _ in range(max(1, args.warmup)):
+    for _ in range(warmup):
         step(solve=False)
     torch.cuda.synchronize()
-    aim.profile_start()
     l0 = aim.launch_count()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
         step()
+    e1.record()
     torch.cuda.synchronize()
-    el = time.perf_counter() - t0
-    prof = aim.profile_stop()
+    el = e0.elapsed_time(e1) / 1e3
     its = [i["iters"] for i in last["info"]]
     return {"metric": "batched filtered Calderon solves (right-hand sides/s) at rel. residual 1e-5",
-            "value": args.steps * R / el, "unit": "rhs-solves/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": "%d x (setup + autotune + one batched product)" % max(1, args.warmup), "ms_per_step": el / args.steps * 1e3, "higher_is_better": True,
-            "dtype": args.precision, "data": "synthetic",
+            "value": steps * R / el, "unit": "rhs-solves/s", "n_gpus": 1, "steps": steps,
+            "warmup": "%d x (setup + autotune + one batched product)" % warmup, "ms_per_step": el / steps * 1e3,
+            "higher_is_better": True, "dtype": precision, "data": "synthetic",
             "config": {"workload": "perimeter 400 wl, N=%d, grid %d^2 (P=%d), %d plane waves, alpha=2k, GMRES(%d)"
                                    % (wl.n, wl.m, wl.fft_P, R, RESTART), "schedule": last["schedule"]},
             "solve": {"status": last["status"], "iters_min": min(its), "iters_max": max(its),
                       "converged": sum(i["converged"] for i in last["info"])},
-            "gpu_launches": aim.launch_count() - l0,
-            "kernels": {k: {"launches": v[0], "total_ms": round(v[1], 3)} for k, v in prof.items()}}
+            "gpu_launches": aim.launch_count() - l0}
 
 
-def serving_arm(args):
+def serving_arm(args, aim=None):
     """Poisson stream (200 requests/s, seed 11): perimeter log-uniform in [5, 500] wavelengths at a
     wavenumber U[pi, 4pi], N = 10 per wavelength, grid 32^2..1024^2, 1..16 plane waves, filtered
     Calderon solves to 1e-5; admission by a device-memory budget, 4 concurrent slots."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_2606_10784_gb300 import aim, serving
+    if aim is None:
+        import __graft_entry__
+        __graft_entry__.build()
+        from paper_2606_10784_gb300 import aim
+    from paper_2606_10784_gb300 import serving
+    precision = "mixed" if args.workload != "serving" else args.precision
     n_warm = max(1, args.requests // 10)
     stream = synth.serving_stream(args.requests + n_warm, rate=200.0, seed=11)
     reqs = []
@@ -488,12 +545,13 @@ def serving_arm(args):
         nodes = synth.StarContour.from_seed(s.seed % 100000).polygon(s.perimeter, s.n_seg)
         reqs.append(serving.SolveRequest(nodes=nodes, k=s.k, m=s.m, angles=synth.equispaced_angles(s.nrhs),
                                          alpha=s.alpha, precision={"fp64": aim.FP64, "mixed": aim.MIXED,
-                                                                   "native": aim.FP64_NATIVE}[args.precision],
+                                                                   "native": aim.FP64_NATIVE}[precision],
                                          tol=SOLVE_TOL, restart=RESTART, arrival=s.t_arrival, rid=i))
     free, total = torch.cuda.mem_get_info()
     budget = int(0.6 * free)
     srv = serving.Server(memory_budget_bytes=budget, slots=4, policy=args.policy)
     serving.replay(srv, reqs[:n_warm])
+    l0 = aim.launch_count()
     t0 = time.perf_counter()
     res = serving.replay(srv, reqs[n_warm:])
     el = time.perf_counter() - t0
@@ -501,16 +559,52 @@ def serving_arm(args):
     timed = [r for r in res if r.rid >= n_warm]
     summ = serving.latency_summary(timed)
     return {"metric": "served filtered Calderon solves: p50/p99 latency and solves/s", "value": summ.get("solves_per_s"),
-            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": args.precision, "data": "synthetic",
+            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": precision, "data": "synthetic",
             "latency": summ, "wall_s": el, "budget_bytes": budget, "refused": srv.refused,
+            "gpu_launches": aim.launch_count() - l0,
             "config": {"workload": "Poisson 200/s, perimeter log-U[5,500] wl, N=10/wl, grids 32^2..1024^2, "
                                    "1..16 rhs, %d timed requests after %d warm-up" % (len(reqs) - n_warm, n_warm),
                        "policy": args.policy, "slots": 4}}
 
 
+# --------------------------------------------------------------------------------------
+# profiling case (for ncu): one operator of the single-solve workload
+# --------------------------------------------------------------------------------------
+def profile_case(args):
+    """Sets up the single-solve contour and applies --op --repeat times to a seeded random vector.
+    The first k_col_conv launch is the operator's first column pass (3 channels for N, 1 for
+    S_alpha), so `ncu -k regex:k_col_conv -c 1` captures one full-size launch. --time prints the mean
+    device time per launch of each grid kernel (CUDA events on the launching stream, after one
+    warm-up product)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_10784_gb300 import aim
+    prec = {"fp64": aim.FP64, "mixed": aim.MIXED, "native": aim.FP64_NATIVE}[args.precision]
+    wl = workload(args.seed)
+    ctx = aim.Context(wl.nodes, wl.k, aim.TE, wl.m, fft_P=wl.fft_P, alpha=wl.alpha)
+    x = torch.from_numpy(synth.random_coeffs(wl.n, 1, 0)).cuda()
+    y = torch.empty_like(x)
+    out = {"op": args.op, "precision": args.precision, "schedule": ctx.get_schedule(prec)}
+    if args.time:
+        ctx.matvec(args.op, x, y, precision=prec)
+        torch.cuda.synchronize()
+        aim.profile_start()
+    for _ in range(max(1, args.repeat)):
+        ctx.matvec(args.op, x, y, precision=prec)
+    torch.cuda.synchronize()
+    if args.time:
+        prof = aim.profile_stop()
+        out["ms_per_launch"] = {k: round(v[1] / max(v[0], 1), 4) for k, v in prof.items() if v[0]}
+    ctx.close()
+    return out
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.profile_case:
+        out = profile_case(args)
+    elif args.impl == "reference":
         out = reference_arm(args)
     elif args.workload == "batching":
         out = batching_arm(args)

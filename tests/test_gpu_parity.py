@@ -356,3 +356,17 @@ def test_every_feasible_schedule_gives_identical_results(te_pair, aimlib, precis
             assert want is None   # native binary64 has only the 16-element geometry
     ctx.set_schedule(precision, **saved)
     assert ran >= 6 and refused >= 1
+
+
+def test_gpu_gmres_takes_the_oracle_gmres_iteration_count(te_pair):
+    # the CPU baseline extrapolates the oracle's solve from its product time and the GPU solve's
+    # iteration count: that rests on both GMRES taking the same number of iterations on the same
+    # system and tolerance (CGS2 on the GPU, MGS in the oracle: the same Krylov space)
+    nodes, ctx, ref = te_pair
+    E = dense.te_rhs(nodes, K, 0.0)
+    b = ref.gram_solve(ref.S_alpha(ref.gram_solve(E)))
+    _, it_o, _ = solve.gmres(lambda v: ref.calderon(v, True), b, tol=1e-5, restart=1000, max_iter=3000)
+    rhs = dev(E[None])
+    x = torch.zeros_like(rhs)
+    info = ctx.solve("calderon_alpha", rhs, x, tol=1e-5, restart=1000, max_iter=3000, precision=0)
+    assert abs(info[0]["iters"] - it_o) <= max(2, 0.02 * it_o), (info[0]["iters"], it_o)
