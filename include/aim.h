@@ -119,7 +119,19 @@ typedef struct {
   double near_radius;
 } aim_stencil;
 
-/* Filter (Sec. III-B): keep spectral bins with kappa <= alpha; requires alpha > k. */
+/* Filter of the "alpha" operators (S^alpha, N^alpha, the filtered Calderon products, the TM
+ * filtered EFIE); requires alpha > k. `enabled` selects how the filtered kernel is made:
+ *   AIM_FILTER_NONE       no filter: the alpha operators equal the unfiltered ones without their
+ *                         near-field correction;
+ *   AIM_FILTER_NUMERICAL  the paper's numerical filter (Sec. III-B, Eq. 10): the spectrum of the
+ *                         grid kernel F(c_grid), self term zeroed (Sec. III-C), truncated to the
+ *                         disc kappa <= alpha, kappa = 2 pi sqrt(p~^2 + q~^2)/(P eps);
+ *   AIM_FILTER_ANALYTIC   the analytically filtered kernel g^alpha of Eq. 6 sampled at the grid
+ *                         offsets, g^alpha(eps sqrt(i~^2 + j~^2)), and transformed: the AIM form of
+ *                         the analytic filter the paper compares with (Fig. 1a, Figs. 2-3). Its
+ *                         samples cost a principal-value integral each (FP64, about alpha r / 8
+ *                         panels of 20 nodes at distance r); setup time grows like P^3. */
+enum { AIM_FILTER_NONE = 0, AIM_FILTER_NUMERICAL = 1, AIM_FILTER_ANALYTIC = 2 };
 typedef struct {
   int enabled;
   double alpha;
@@ -154,6 +166,7 @@ typedef struct {
   long long nnz_near;  /* near-field correction entries */
   size_t device_bytes; /* device memory held by the context */
   double setup_seconds;
+  int filter_kind;     /* AIM_FILTER_NONE, AIM_FILTER_NUMERICAL or AIM_FILTER_ANALYTIC */
 } aim_info;
 
 typedef struct aim_ctx aim_ctx;
@@ -231,6 +244,23 @@ aim_status aim_matvec(aim_ctx* ctx, aim_op op, int nrhs, const void* x, void* y,
  * v outside it are returned as zero. */
 aim_status aim_grid_product(aim_ctx* ctx, int filtered, int nrhs, const void* u, void* v,
                             int precision, void* stream);
+
+/* Grid kernel tables, for comparing the numerical filter with the analytic one (Sec. III-B,
+ * Fig. 1). Each table is the (H+1) x (H+1) quarter, H = fft_P/2, of an array that is even in both
+ * indices, written row-major as complex128 (element [a][b] at a*(H+1) + b; host or device `out`).
+ *   AIM_TABLE_SPECTRUM            F(c_grid)[p][q]: the DFT of the grid kernel samples
+ *                                 g(eps sqrt(i~^2 + j~^2)) with the self term set to zero
+ *                                 (Sec. III-A, III-C), as the unfiltered products use it;
+ *   AIM_TABLE_SPECTRUM_FILTERED   the spectrum the filtered products use: F(c_grid) truncated to
+ *                                 kappa <= alpha (Eq. 10), or the analytic one (AIM_FILTER_ANALYTIC);
+ *   AIM_TABLE_ANALYTIC_SAMPLES    g^alpha(eps sqrt(i^2 + j^2)) of Eq. 6 at offset [i][j] (computed
+ *                                 on the call's stream; needs a context set up with a filter);
+ *   AIM_TABLE_ANALYTIC_SPECTRUM   the DFT of those samples (Fig. 1a; computed likewise).
+ * The call synchronises `stream`. Errors: AIM_EINVAL (unknown table, null pointer), AIM_ESTATE
+ * (analytic tables of a context without a filter radius), AIM_ENOMEM, AIM_ECUDA. */
+enum { AIM_TABLE_SPECTRUM = 0, AIM_TABLE_SPECTRUM_FILTERED = 1, AIM_TABLE_ANALYTIC_SAMPLES = 2,
+       AIM_TABLE_ANALYTIC_SPECTRUM = 3 };
+aim_status aim_kernel_table(aim_ctx* ctx, int which, void* out, void* stream);
 
 /* Size of the scratch array behind aim_grid_product_noalloc (bytes). */
 #define AIM_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)

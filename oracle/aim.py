@@ -12,7 +12,9 @@ Steps, in the paper's order (Sec. III):
    c_grid is the grid kernel mirrored about its last row and column, u is zero-padded, and
    v = [F^-1(F(c_grid) .* F(b))]_restr.
 4. Sec. III-B: the filter is a circular truncation of F(c_grid) at radius alpha,
-   giving F(c_grid^alpha); Eq. 10 then uses it in place of F(c_grid).
+   giving F(c_grid^alpha); Eq. 10 then uses it in place of F(c_grid). For comparison
+   (Fig. 1a) the analytically filtered kernel g^alpha of Eq. 6 can instead be sampled on
+   the grid and transformed (filter_kind="analytic").
 5. Sec. III-C: the self interaction of G_grid is set to zero (before the FFT and mask).
 
 Readings taken where the paper leaves a choice (all listed in the design notes):
@@ -165,6 +167,20 @@ def grid_kernel(k: float, eps: float, P: int) -> np.ndarray:
     return c
 
 
+def analytic_grid_kernel(k: float, eps: float, P: int, alpha: float) -> np.ndarray:
+    """The analytically filtered kernel of Eq. 6 sampled on the P x P periodic cell:
+    c^alpha_an[i,j] = g^alpha(eps*sqrt(i~^2 + j~^2)). g^alpha is regular at the origin, so the
+    self term keeps its value g^alpha(0) (nothing to zero, Sec. III-C). Each distinct distance is
+    evaluated once (the cell is even in both indices and symmetric under i <-> j)."""
+    t = np.abs(signed_index(P))
+    H = P // 2
+    quarter = np.zeros((H + 1, H + 1), dtype=np.complex128)
+    for i in range(H + 1):
+        for j in range(i, H + 1):
+            quarter[i, j] = quarter[j, i] = special.filtered_green(k, alpha, eps * math.hypot(i, j))
+    return quarter[t[:, None], t[None, :]]
+
+
 def dft_matrix(P: int) -> np.ndarray:
     j = np.arange(P)
     return np.exp(-2j * math.pi * np.outer(j, j) / P)
@@ -302,7 +318,7 @@ def aim_entries(Pt: sp.csr_matrix, Ps: sp.csr_matrix, t: np.ndarray, m: int, row
 # Operators
 # --------------------------------------------------------------------------------------
 class _AimBase:
-    def _grid_setup(self, nodes, k, m, P, s, p, alpha, L, near_radius, direct_dft):
+    def _grid_setup(self, nodes, k, m, P, s, p, alpha, L, near_radius, direct_dft, filter_kind="numerical"):
         self.nodes = np.asarray(nodes, dtype=np.float64)
         self.n = self.nodes.shape[0]
         self.k, self.m, self.P, self.s, self.p, self.alpha = float(k), int(m), int(P), int(s), int(p), float(alpha)
@@ -314,8 +330,15 @@ class _AimBase:
         self.direct = (P <= 256) if direct_dft is None else bool(direct_dft)
         self.c = grid_kernel(self.k, self.eps, self.P)
         self.Chat = dft2(self.c, self.direct)
+        self.filter_kind = filter_kind
         self.mask = filter_mask(self.P, self.eps, self.alpha)
-        self.Chat_alpha = self.Chat * self.mask
+        if filter_kind == "numerical":          # Sec. III-B: circular truncation of F(c_grid) (Eq. 10)
+            self.Chat_alpha = self.Chat * self.mask
+        elif filter_kind == "analytic":         # Eq. 6 sampled on the grid, then transformed
+            self.c_an = analytic_grid_kernel(self.k, self.eps, self.P, self.alpha)
+            self.Chat_alpha = dft2(self.c_an, self.direct)
+        else:
+            raise ValueError("filter_kind must be 'numerical' or 'analytic'")
         self._c_alpha = None
 
     @property
@@ -359,8 +382,9 @@ class TEOperators(_AimBase):
     """TE, P1 hats, Galerkin: S, S^alpha (Eq. 10), N (Maue form), G, and the Calderon products (Eq. 3)."""
 
     def __init__(self, nodes, k, m, P, s=4, p=4, alpha=None, L=None, near_radius=None, direct_dft=None,
-                 near=True):
-        self._grid_setup(nodes, k, m, P, s, p, alpha if alpha is not None else 8.0 * k, L, near_radius, direct_dft)
+                 near=True, filter_kind="numerical"):
+        self._grid_setup(nodes, k, m, P, s, p, alpha if alpha is not None else 8.0 * k, L, near_radius, direct_dft,
+                         filter_kind)
         self.proj = te_projections(self.nodes, self.p, self.L, self.eps, self.m, self.s)
         self.G = sp.csc_matrix(geometry.gram_dense(self.nodes)) if self.n <= 2048 else self._gram_sparse()
         self.near_rows = self.near_cols = None
@@ -436,8 +460,9 @@ class TMOperators(_AimBase):
     """TM, pulse basis, midpoint collocation: Z = j k eta S (unfiltered + near field) and Z^alpha."""
 
     def __init__(self, nodes, k, m, P, s=4, p=4, alpha=None, L=None, near_radius=None, direct_dft=None,
-                 eta=1.0, near=True):
-        self._grid_setup(nodes, k, m, P, s, p, alpha if alpha is not None else 8.0 * k, L, near_radius, direct_dft)
+                 eta=1.0, near=True, filter_kind="numerical"):
+        self._grid_setup(nodes, k, m, P, s, p, alpha if alpha is not None else 8.0 * k, L, near_radius, direct_dft,
+                         filter_kind)
         self.eta = float(eta)
         self.proj = tm_projections(self.nodes, self.p, self.L, self.eps, self.m, self.s)
         self.CZ = sp.csr_matrix((self.n, self.n), dtype=np.complex128)

@@ -6,6 +6,7 @@ TEST INFRASTRUCTURE ONLY: used by tests, smoke() and the benchmark's CPU baselin
 * Circle eigenvalues of S and N and of the analytically filtered S^alpha (Sec. II,
   Eqs. 4-6), derived with Graf's addition theorem; pinned in the tests against the
   dense operators on regular polygons and against each other (lambda_n mu_n -> 1/4).
+* The analytically filtered kernel g^alpha of Eq. 6 at a distance (a principal-value integral).
 * PEC circular-cylinder series currents (TM, TE) for the same time convention.
 
 Pins: g against the small-argument expansion of H0^(2); Gauss rules against exact
@@ -14,6 +15,7 @@ polynomial moments and the log moment; closed forms against the dense oracle ope
 from __future__ import annotations
 
 import math
+import warnings
 
 import numpy as np
 from scipy import integrate, special
@@ -97,6 +99,37 @@ def circle_lambda_filtered(n: int, k: float, a: float, alpha: float) -> complex:
             val, _ = integrate.quad(lambda s: f(s) / (s - k), lo, hi, limit=400, epsabs=1e-14, epsrel=1e-13)
         pv += val
     return a * pv - 0.5j * math.pi * a * special.jv(n, k * a) ** 2
+
+
+def filtered_green(k: float, alpha: float, r: float) -> complex:
+    """The analytically filtered kernel g^alpha of Eq. 6 at distance r >= 0.
+
+    Eq. 6 writes g^alpha = -(j/4) H0^(2)(kr) - (1/2 pi) int_alpha^inf J0(sr) s/(s^2-k^2) ds. With the
+    integral representation PV int_0^inf J0(sr) s/(s^2-k^2) ds = -(pi/2) Y0(kr) (DLMF 10.9, the
+    same identity behind circle_lambda_filtered) and H0^(2) = J0 - j Y0, the Y0 terms cancel:
+        g^alpha(r) = -(j/4) J0(kr) + (1/2 pi) PV int_0^alpha J0(sr) s/(s^2-k^2) ds,
+    a finite integral, regular at r = 0 (Sec. III-C: the filtered kernel has no singularity).
+    The principal value is QUADPACK's Cauchy-weight rule on the panel that holds s = k; the range is
+    cut into panels of about two oscillations of J0(sr).
+    """
+    r = float(r)
+    f = lambda s: special.j0(s * r) * s / (s + k)
+    edges = list(np.linspace(0.0, alpha, 2 + int(alpha * r / 4.0)))
+    # keep s = k strictly inside a panel
+    for i in range(1, len(edges) - 1):
+        if abs(edges[i] - k) < 1e-6 * k:
+            del edges[i]
+            break
+    pv = 0.0
+    with np.errstate(all="ignore"), warnings.catch_warnings():
+        warnings.simplefilter("ignore", integrate.IntegrationWarning)
+        for lo, hi in zip(edges[:-1], edges[1:]):
+            if lo < k < hi:
+                val, _ = integrate.quad(f, lo, hi, weight="cauchy", wvar=k, limit=400, epsabs=1e-15, epsrel=1e-13)
+            else:
+                val, _ = integrate.quad(lambda s: f(s) / (s - k), lo, hi, limit=400, epsabs=1e-15, epsrel=1e-13)
+            pv += val
+    return complex(pv / (2.0 * math.pi), -0.25 * special.j0(k * r))
 
 
 def tm_cylinder_current(phi: np.ndarray, ka: float, a: float, theta: float = 0.0, eta: float = 1.0,

@@ -22,6 +22,8 @@ TM, TE = 0, 1
 (OP_S, OP_S_ALPHA, OP_N, OP_CALDERON, OP_CALDERON_ALPHA, OP_GRAM_INV, OP_EFIE, OP_EFIE_ALPHA, OP_N_ALPHA,
  OP_CALDERON_ALPHA2) = range(10)
 FP64, MIXED, FP64_NATIVE = 0, 1, 2
+FILTER_NONE, FILTER_NUMERICAL, FILTER_ANALYTIC = 0, 1, 2
+TABLE_SPECTRUM, TABLE_SPECTRUM_FILTERED, TABLE_ANALYTIC_SAMPLES, TABLE_ANALYTIC_SPECTRUM = 0, 1, 2, 3
 
 OPS = {"S": OP_S, "S_alpha": OP_S_ALPHA, "N": OP_N, "calderon": OP_CALDERON,
        "calderon_alpha": OP_CALDERON_ALPHA, "gram_inv": OP_GRAM_INV, "efie": OP_EFIE, "efie_alpha": OP_EFIE_ALPHA,
@@ -60,7 +62,7 @@ class Info(ctypes.Structure):
                 ("quad_p", ctypes.c_int), ("k", ctypes.c_double), ("L", ctypes.c_double), ("eps", ctypes.c_double),
                 ("alpha", ctypes.c_double), ("n_active", ctypes.c_int), ("row_lo", ctypes.c_int),
                 ("row_hi", ctypes.c_int), ("nnz_near", ctypes.c_longlong), ("device_bytes", ctypes.c_size_t),
-                ("setup_seconds", ctypes.c_double)]
+                ("setup_seconds", ctypes.c_double), ("filter_kind", ctypes.c_int)]
 
 
 class Schedule(ctypes.Structure):
@@ -131,6 +133,8 @@ def lib() -> ctypes.CDLL:
     L.aim_query_solve_bytes.restype = i
     L.aim_grid_product_noalloc.argtypes = [vp, i, i, vp, vp, i, vp]
     L.aim_grid_product_noalloc.restype = i
+    L.aim_kernel_table.argtypes = [vp, i, vp, vp]
+    L.aim_kernel_table.restype = i
     L.aim_autotune.argtypes = [vp, i, i, vp, ctypes.POINTER(Schedule)]
     L.aim_autotune.restype = i
     L.aim_set_schedule.argtypes = [vp, i, ctypes.POINTER(Schedule)]
@@ -218,9 +222,10 @@ class Context:
     """One AIM operator set on the current CUDA device (wraps aim_ctx*)."""
 
     def __init__(self, nodes, k: float, form: int, m: int, fft_P: int = 0, L: float = 0.0, s: int = 4,
-                 quad_p: int = 4, near_radius: float = 0.0, alpha: Optional[float] = None, stream=None):
+                 quad_p: int = 4, near_radius: float = 0.0, alpha: Optional[float] = None, stream=None,
+                 filter_kind: int = FILTER_NUMERICAL):
         g, keep = _geometry(nodes, form, quad_p)
-        flt = Filter(1 if alpha is not None else 0, float(alpha) if alpha is not None else 0.0)
+        flt = Filter(int(filter_kind) if alpha is not None else FILTER_NONE, float(alpha) if alpha is not None else 0.0)
         h = ctypes.c_void_p()
         _check(lib().aim_setup(ctypes.byref(g), float(k), ctypes.byref(Grid(int(m), float(L), int(fft_P))),
                                ctypes.byref(Stencil(int(s), float(near_radius))), ctypes.byref(flt),
@@ -272,6 +277,11 @@ class Context:
         sc = Schedule()
         _check(lib().aim_get_schedule(self._h, int(precision), ctypes.byref(sc)), "aim_get_schedule")
         return sc.as_dict()
+
+    def kernel_table(self, which: int, out, stream=None):
+        """(H+1) x (H+1) grid kernel table (aim_kernel_table): spectra or analytic samples."""
+        _check(lib().aim_kernel_table(self._h, int(which), _ptr(out), _stream_ptr(stream)), "aim_kernel_table")
+        return out
 
     def rhs_planewave(self, angles, out, stream=None):
         ang = np.ascontiguousarray(np.asarray(angles, dtype=np.float64).reshape(-1))

@@ -233,6 +233,8 @@ void gauss_legendre01(int n, std::vector<double>* x, std::vector<double>* w);
 // ------------------------------------------------------------------------------------
 // kernel samples -> near-field entries -> spectrum F(c) and its truncation (in that order)
 aim_status device_spectra_and_near(aim_ctx* ctx, const HostSetup& hs, cudaStream_t st);
+// the grid kernel tables of aim_kernel_table (natural order, (H+1)^2 complex128, device `out`)
+aim_status kernel_table(aim_ctx* ctx, int which, double2* out, cudaStream_t st);
 aim_status device_rhs_planewave(aim_ctx* ctx, int nrhs, const double* angles_dev, double2* out, cudaStream_t st);
 
 // ------------------------------------------------------------------------------------

@@ -251,7 +251,10 @@ static aim_status validate(const aim_geometry* g, double k, const aim_grid* grid
   if (st->s < 2 || st->s > 12) return fail(AIM_EINVAL, "stencil s must be in 2..12");
   if (grid->fft_P != 0 && (!is_pow2(grid->fft_P) || grid->fft_P < 2 * grid->m - 1))
     return fail(AIM_EINVAL, "fft_P must be a power of two >= 2m-1");
-  if (f && f->enabled && !(f->alpha > k)) return fail(AIM_EINVAL, "filter radius alpha must exceed k");
+  if (f && (f->enabled < AIM_FILTER_NONE || f->enabled > AIM_FILTER_ANALYTIC))
+    return fail(AIM_EINVAL, "filter kind must be AIM_FILTER_NONE, AIM_FILTER_NUMERICAL or AIM_FILTER_ANALYTIC");
+  if (f && f->enabled && !(f->alpha > k) && std::isfinite(f->alpha)) return fail(AIM_EINVAL, "filter radius alpha must exceed k");
+  if (f && f->enabled && !std::isfinite(f->alpha)) return fail(AIM_EINVAL, "filter radius alpha must be finite");
   for (int i = 0; i < 2 * g->n_seg; ++i)
     if (!std::isfinite(g->xy[i])) return fail(AIM_EINVAL, "non-finite vertex coordinate");
   return AIM_OK;
@@ -281,7 +284,7 @@ static aim_status derive_params(aim_ctx* ctx, const aim_geometry* geometry, doub
   ctx->L = grid->half_side_L > 0.0 ? grid->half_side_L : host_grid_half_side(geometry->xy, ctx->n, ctx->m, ctx->s);
   ctx->eps = 2.0 * ctx->L / (ctx->m - 1);
   ctx->near_radius = stencil->near_radius > 0.0 ? stencil->near_radius : ctx->s * ctx->eps;
-  ctx->filter_enabled = filter && filter->enabled;
+  ctx->filter_enabled = filter ? filter->enabled : AIM_FILTER_NONE;
   ctx->alpha = ctx->filter_enabled ? filter->alpha : 0.0;
   return AIM_OK;
 }
@@ -371,7 +374,32 @@ aim_status aim_get_info(const aim_ctx* ctx, aim_info* info) {
   info->device_bytes = ctx->device_bytes + ctx->inter_bytes + ctx->vact_bytes + ctx->vec_ws_bytes +
                        2 * ctx->stage_bytes + ctx->kry_bytes + ctx->red_bytes;
   info->setup_seconds = ctx->setup_seconds;
+  info->filter_kind = ctx->filter_enabled;
   return AIM_OK;
+}
+
+aim_status aim_kernel_table(aim_ctx* ctx, int which, void* out, void* stream) {
+  if (!ctx || !out) return fail(AIM_EINVAL, "bad argument");
+  if (which < AIM_TABLE_SPECTRUM || which > AIM_TABLE_ANALYTIC_SPECTRUM) return fail(AIM_EINVAL, "unknown kernel table");
+  AIM_TRY(check_device(ctx));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t bytes = (size_t)(ctx->H + 1) * (ctx->H + 1) * sizeof(double2);
+  const bool dev = device_pointer(out);
+  double2* buf = static_cast<double2*>(out);
+  if (!dev) {
+    void* p = nullptr;
+    AIM_CUDA_TRY(cudaMalloc(&p, bytes));
+    buf = static_cast<double2*>(p);
+  }
+  aim_status s = kernel_table(ctx, which, buf, st);
+  if (s == AIM_OK && !dev) {
+    const cudaError_t e = cudaMemcpyAsync(out, buf, bytes, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) s = fail(AIM_ECUDA, std::string("kernel table copy: ") + cudaGetErrorString(e));
+  }
+  const cudaError_t es = cudaStreamSynchronize(st);
+  if (s == AIM_OK && es != cudaSuccess) s = fail(AIM_ECUDA, std::string("kernel table: ") + cudaGetErrorString(es));
+  if (!dev) cudaFree(buf);
+  return s;
 }
 
 aim_status aim_reserve(aim_ctx* ctx, int nrhs, int precision) {

@@ -68,6 +68,39 @@ __device__ void bessel_j0y0(double x, double* J0, double* Y0) {
   *Y0 = amp * (Pv * sw + Qv * cw);
 }
 
+// J0 alone, by the same three branches (for the filtered kernel's integrand)
+__device__ double bessel_j0(double x) {
+  if (x < 8.0) return j0(x);
+  if (x < 25.0) {
+    const int nstart = 2 * (int)((x + 30.0 + 8.0 * cbrt(x)) * 0.5);
+    double jp1 = 0.0, jn = 1.0, s_even = 0.0;
+    for (int nn = nstart; nn > 0; --nn) {
+      const double jm1 = (2.0 * nn / x) * jn - jp1;
+      jp1 = jn;
+      jn = jm1;
+      const int kk = nn - 1;
+      if (kk > 0 && (kk & 1) == 0) s_even += jn;
+      if (fabs(jn) > 1e100) {
+        jn *= 1e-100; jp1 *= 1e-100; s_even *= 1e-100;
+      }
+    }
+    return jn / (jn + 2.0 * s_even);
+  }
+  double a = 1.0, Pv = 1.0, Qv = 0.0, xp = 1.0;
+  for (int kk = 1; kk <= 24; ++kk) {
+    a *= -(double)((2 * kk - 1) * (2 * kk - 1)) / (8.0 * kk);
+    xp *= x;
+    const double term = a / xp;
+    if (kk & 1) Qv += ((kk >> 1) & 1 ? -term : term);
+    else Pv += ((kk >> 1) & 1 ? -term : term);
+  }
+  double sx, cx;
+  sincos(x, &sx, &cx);
+  const double cw = (cx + sx) * 0.70710678118654752440;
+  const double sw = (sx - cx) * 0.70710678118654752440;
+  return sqrt(2.0 / (M_PI * x)) * (Pv * cw - Qv * sw);
+}
+
 // g(r) = -(j/4) H0^(2)(kr) = -(j/4)(J0 - j Y0) = (-Y0/4, -J0/4)
 __device__ __forceinline__ double2 green(double k, double r) {
   double J, Y;
@@ -119,9 +152,11 @@ __device__ __forceinline__ float4 split_df(double2 v) {
 // live[q'] = 0 when the mask zeroes column q' entirely. kappa(p, q') >= kappa(0, q') holds in
 // floating point as well (sqrt is exact on the perfect square q'^2 and monotone, and both are
 // scaled by the same factor), so the column has a kept entry exactly when its p = 0 entry is kept.
-__global__ void k_pack_spectrum(const double2* C, int H, int P, double eps, double alpha, int filter,
-                                double2* specU, double2* specA, float2* specUf, float2* specAf, float4* specUdf,
-                                float4* specAdf, int* live) {
+// CA (may be null): the transform of the analytically filtered samples, which then becomes the
+// filtered spectrum as it is (no mask; every column live).
+__global__ void k_pack_spectrum(const double2* C, const double2* CA, int H, int P, double eps, double alpha,
+                                int filter, double2* specU, double2* specA, float2* specUf, float2* specAf,
+                                float4* specUdf, float4* specAdf, int* live) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long total = (long long)(H + 1) * (H + 1);
   if (t >= total) return;
@@ -133,12 +168,12 @@ __global__ void k_pack_spectrum(const double2* C, int H, int P, double eps, doub
   const bool keep = !filter || kappa <= alpha;
   specU[t] = v;
   specUf[t] = float2{(float)v.x, (float)v.y};
-  const double2 va = keep ? v : double2{0.0, 0.0};
+  const double2 va = CA != nullptr ? CA[(size_t)p * (H + 1) + qq] : keep ? v : double2{0.0, 0.0};
   specA[t] = va;
   specAf[t] = float2{(float)va.x, (float)va.y};
   specUdf[t] = split_df(v);
   specAdf[t] = split_df(va);
-  if (off == 0) live[qq] = keep ? 1 : 0;   // p = 0
+  if (off == 0) live[qq] = (CA != nullptr || keep) ? 1 : 0;   // p = 0
 }
 
 // ------------------------------------------------------------------------------------
@@ -148,6 +183,46 @@ struct QuadTables {
   double x10[10], w10[10], x12[12], w12[12], x16[16], w16[16], x20[20], w20[20], x24[24], w24[24];
 };
 __constant__ QuadTables c_quad;
+
+// The analytically filtered kernel of Eq. 6 on the grid: samp[i (H+1) + j] = g^alpha(eps sqrt(i^2+j^2)).
+// With PV int_0^inf J0(sr) s/(s^2-k^2) ds = -(pi/2) Y0(kr), Eq. 6 becomes
+//     g^alpha(r) = -(j/4) J0(kr) + (1/2 pi) PV int_0^alpha J0(sr) s/(s^2-k^2) ds,
+// regular at r = 0, so the self term keeps its value (Sec. III-C). The pole at s = k is taken out:
+//     PV int = int_0^alpha [J0(sr) s - J0(kr) k]/((s-k)(s+k)) ds + (J0(kr)/2) ln((alpha-k)/(alpha+k)),
+// and the smooth remainder runs over panels of [0,k] and [k,alpha] no wider than 8/r (about 1.3
+// oscillations of J0(sr)), 20 Gauss-Legendre nodes each (no node falls on s = k). One warp per
+// sample: lanes take the nodes in turn and a fixed xor-shuffle tree adds them.
+constexpr double kFilterPanelPhase = 8.0;
+
+__global__ void k_sample_filtered_kernel(double2* samp, int H, double eps, double k, double alpha) {
+  const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const long long total = (long long)(H + 1) * (H + 1);
+  if (wid >= total) return;   // whole warps
+  const int i = (int)(wid / (H + 1)), j = (int)(wid - (long long)i * (H + 1));
+  const double r = eps * sqrt((double)i * i + (double)j * j);
+  const double Jk = bessel_j0(k * r);
+  const int n1 = max(1, (int)ceil(k * r / kFilterPanelPhase));
+  const int n2 = max(1, (int)ceil((alpha - k) * r / kFilterPanelPhase));
+  const double w1 = k / n1, w2 = (alpha - k) / n2;
+  const int total_nodes = (n1 + n2) * 20;
+  double acc = 0.0;
+  for (int q = lane; q < total_nodes; q += 32) {
+    const int pan = q / 20, node = q - pan * 20;
+    const double a0 = pan < n1 ? pan * w1 : k + (pan - n1) * w2;
+    const double w = pan < n1 ? w1 : w2;
+    const double sv = a0 + w * c_quad.x20[node];
+    const double f = (bessel_j0(sv * r) * sv - Jk * k) / ((sv - k) * (sv + k));
+    acc = fma(w * c_quad.w20[node], f, acc);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+  if (lane == 0) {
+    const double pv = acc + 0.5 * Jk * log((alpha - k) / (alpha + k));
+    samp[wid] = double2{pv / (2.0 * M_PI), -0.25 * Jk};
+  }
+}
+
 
 __device__ __forceinline__ double2 cmadd(double2 acc, double s, double2 g) {
   return double2{fma(s, g.x, acc.x), fma(s, g.y, acc.y)};
@@ -517,6 +592,75 @@ struct DeviceTemp {
   }
 };
 
+// In-place 2-D DFT of an even-symmetric P x P array held as its (H+1) x (H+1) quarter.
+static aim_status even_dft_2d(aim_ctx* ctx, double2* a, cudaStream_t st) {
+  const int H = ctx->H, P = ctx->P;
+  const size_t sm = (size_t)P * sizeof(double2);
+  constexpr int NB = 4;
+  const int th = std::max(64, std::min(1024, (P / 4 + NB - 1) / NB));
+  if (sm > 48 * 1024)
+    AIM_CUDA_TRY(cudaFuncSetAttribute(k_even_line_dft<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  for (int by_rows = 1; by_rows >= 0; --by_rows) {
+    {
+      ProfScope ps(K_SETUP_DFT, st);
+      k_even_line_dft<NB><<<H + 1, th, sm, st>>>(a, H, ctx->logP, ctx->tw, by_rows);
+    }
+    AIM_CUDA_TRY(cudaGetLastError());
+  }
+  return AIM_OK;
+}
+
+// g^alpha of Eq. 6 at the grid offsets (i, j), i, j = 0..H, into `out` ((H+1)^2, device).
+aim_status analytic_samples(aim_ctx* ctx, double2* out, cudaStream_t st) {
+  if (!(ctx->alpha > ctx->k)) return fail(AIM_ESTATE, "the analytic filter needs alpha > k (set up with a filter)");
+  AIM_TRY(upload_quad_tables());
+  const long long total = (long long)(ctx->H + 1) * (ctx->H + 1);
+  const int tpb = 256;
+  const long long blocks = (total * 32 + tpb - 1) / tpb;
+  {
+    ProfScope ps(K_SETUP_SAMPLE, st);
+    k_sample_filtered_kernel<<<(unsigned)blocks, tpb, 0, st>>>(out, ctx->H, ctx->eps, ctx->k, ctx->alpha);
+  }
+  AIM_CUDA_TRY(cudaGetLastError());
+  return AIM_OK;
+}
+
+// Natural-order quarter F[p][q], p, q = 0..H, of a packed spectrum (per column q: even rows, then odd rows).
+__global__ void k_unpack_spectrum(const double2* packed, int H, double2* out) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)(H + 1) * (H + 1);
+  if (t >= total) return;
+  const int p = (int)(t / (H + 1)), q = (int)(t - (long long)p * (H + 1));
+  const int half = H >> 1;
+  const int off = (p & 1) ? half + 1 + (p >> 1) : (p >> 1);
+  out[t] = packed[(size_t)q * (H + 1) + off];
+}
+
+aim_status kernel_table(aim_ctx* ctx, int which, double2* out, cudaStream_t st) {
+  const int H = ctx->H;
+  const long long total = (long long)(H + 1) * (H + 1);
+  const int tpb = 256;
+  switch (which) {
+    case AIM_TABLE_SPECTRUM:
+    case AIM_TABLE_SPECTRUM_FILTERED: {
+      const double2* src = which == AIM_TABLE_SPECTRUM ? ctx->specU : ctx->specA;
+      {
+        ProfScope ps(K_SETUP_PACK, st);
+        k_unpack_spectrum<<<(unsigned)((total + tpb - 1) / tpb), tpb, 0, st>>>(src, H, out);
+      }
+      AIM_CUDA_TRY(cudaGetLastError());
+      return AIM_OK;
+    }
+    case AIM_TABLE_ANALYTIC_SAMPLES:
+      return analytic_samples(ctx, out, st);
+    case AIM_TABLE_ANALYTIC_SPECTRUM:
+      AIM_TRY(analytic_samples(ctx, out, st));
+      return even_dft_2d(ctx, out, st);
+    default:
+      return fail(AIM_EINVAL, "unknown kernel table");
+  }
+}
+
 // Builds spectra and the near field. The kernel samples are needed by both: the near-field
 // AIM entries read them first, then the spectrum transform overwrites them in place.
 aim_status device_spectra_and_near(aim_ctx* ctx, const HostSetup& hs, cudaStream_t st) {
@@ -614,22 +758,13 @@ aim_status device_spectra_and_near(aim_ctx* ctx, const HostSetup& hs, cudaStream
   }
 
   // ---- spectrum: even-symmetric 2-D DFT of the samples, in place, then pack + mask
-  {
-    const size_t sm = (size_t)P * sizeof(double2);
-    constexpr int NB = 4;
-    const int th = std::max(64, std::min(1024, (P / 4 + NB - 1) / NB));
-    if (sm > 48 * 1024)
-      AIM_CUDA_TRY(cudaFuncSetAttribute(k_even_line_dft<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    {
-      ProfScope ps(K_SETUP_DFT, st);
-      k_even_line_dft<NB><<<H + 1, th, sm, st>>>(samp, H, ctx->logP, ctx->tw, 1);
-    }
-    AIM_CUDA_TRY(cudaGetLastError());
-    {
-      ProfScope ps(K_SETUP_DFT, st);
-      k_even_line_dft<NB><<<H + 1, th, sm, st>>>(samp, H, ctx->logP, ctx->tw, 0);
-    }
-    AIM_CUDA_TRY(cudaGetLastError());
+  AIM_TRY(even_dft_2d(ctx, samp, st));
+  // the analytically filtered kernel (Eq. 6) sampled on the grid and transformed, when asked for
+  double2* sampA = nullptr;
+  if (ctx->filter_enabled == AIM_FILTER_ANALYTIC) {
+    AIM_TRY(tmp.alloc(&sampA, nq));
+    AIM_TRY(analytic_samples(ctx, sampA, st));
+    AIM_TRY(even_dft_2d(ctx, sampA, st));
   }
   AIM_TRY(dev_alloc_t(ctx, &ctx->specU, nq));
   AIM_TRY(dev_alloc_t(ctx, &ctx->specA, nq));
@@ -641,7 +776,7 @@ aim_status device_spectra_and_near(aim_ctx* ctx, const HostSetup& hs, cudaStream
   {
     const int tpb = 256;
     ProfScope ps(K_SETUP_PACK, st);
-    k_pack_spectrum<<<(unsigned)((nq + tpb - 1) / tpb), tpb, 0, st>>>(samp, H, P, ctx->eps, ctx->alpha,
+    k_pack_spectrum<<<(unsigned)((nq + tpb - 1) / tpb), tpb, 0, st>>>(samp, sampA, H, P, ctx->eps, ctx->alpha,
                                                                       ctx->filter_enabled, ctx->specU, ctx->specA,
                                                                       ctx->specUf, ctx->specAf, ctx->specUdf,
                                                                       ctx->specAdf, ctx->specA_live);

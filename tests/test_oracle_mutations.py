@@ -201,3 +201,22 @@ def test_planted_shifted_segment_index(monkeypatch):
         return out
     monkeypatch.setattr(aim, "tm_projections", bad)
     assert _tm_pin_fails()
+
+
+def test_planted_sign_of_the_filtered_tail(monkeypatch):
+    # Eq. 6 subtracts the tail beyond alpha; adding it instead flips the sign of the principal-value
+    # part of the regular form; the analytic-filter pin against lambda_n^alpha catches it
+    orig = special.filtered_green
+
+    def bad(k, alpha, r):
+        v = orig(k, alpha, r)
+        return complex(-v.real, v.imag)
+    monkeypatch.setattr(special, "filtered_green", bad)
+    N = 128
+    nodes = synth.circle_polygon(1.0, N)
+    G = geometry.gram_dense(nodes)
+    op = aim.TEOperators(nodes, K, 48, 96, alpha=4 * K, near=False, direct_dft=False, filter_kind="analytic")
+    v = np.ones(N, dtype=np.complex128)
+    lam0 = np.vdot(v, op.S_alpha(v)) / np.vdot(v, G @ v)
+    exact = special.circle_lambda_filtered(0, K, 1.0, 4 * K)
+    assert abs(lam0 - exact) > 0.1 * abs(exact)

@@ -372,6 +372,77 @@ def test_numerical_filter_truncates_beyond_alpha_a(circle_filtered):
 
 
 # --------------------------------------------------------------------------------------
+# The analytic filter of Eq. 6 sampled on the grid (Fig. 1a) against closed forms and the
+# numerical filter
+# --------------------------------------------------------------------------------------
+def test_analytic_filtered_kernel_at_the_origin():
+    # g^alpha(0) = -j/4 + (1/2 pi) PV int_0^alpha s/(s^2-k^2) ds = -j/4 + ln((alpha^2-k^2)/k^2)/(4 pi)
+    for alpha in (2 * K, 8 * K):
+        want = -0.25j + math.log((alpha ** 2 - K ** 2) / K ** 2) / (4 * math.pi)
+        assert abs(special.filtered_green(K, alpha, 0.0) - want) < 1e-13
+
+
+def test_analytic_filtered_kernel_tends_to_the_green_function():
+    # the subtracted tail of Eq. 6 decays like alpha^(-3/2) (J0(sr) ~ (s r)^(-1/2) cos): a factor 8 per 4x alpha
+    for r in (0.3, 1.0):
+        g = special.green(K, np.array([r]))[0]
+        e1 = abs(special.filtered_green(K, 50 * K, r) - g)
+        e2 = abs(special.filtered_green(K, 200 * K, r) - g)
+        assert e2 < 0.25 * e1 and e2 < 5e-5
+
+
+def _circle_modes(nodes, G, N, apply, modes):
+    out = []
+    for n in modes:
+        v = np.exp(1j * n * 2.0 * math.pi * np.arange(N) / N)
+        out.append(np.vdot(v, apply(v)) / np.vdot(v, G @ v))
+    return np.array(out)
+
+
+@pytest.fixture(scope="module")
+def circle_analytic():
+    N = 256
+    nodes = synth.circle_polygon(1.0, N)
+    G = geometry.gram_dense(nodes)
+    ops = {(m, kind): aim.TEOperators(nodes, K, m, 2 * m, alpha=4 * K, near=False, direct_dft=False, filter_kind=kind)
+           for m in (32, 64, 128) for kind in ("analytic", "numerical")}
+    return N, nodes, G, ops
+
+
+def test_analytic_filter_in_aim_converges_to_the_closed_form(circle_analytic):
+    # S^alpha built from g^alpha sampled on the grid: its circle eigenvalues approach lambda_n^alpha
+    # (Eqs. 5-6 with Graf's theorem), across the filtering point alpha a = 4 k a ~ 25
+    N, nodes, G, ops = circle_analytic
+    modes = (0, 5, 10, 20, 30)
+    exact = np.array([special.circle_lambda_filtered(n, K, 1.0, 4 * K) for n in modes])
+    scale = np.abs(exact).max()
+    err = {m: np.abs(_circle_modes(nodes, G, N, ops[(m, "analytic")].S_alpha, modes) - exact).max() / scale
+           for m in (32, 64, 128)}
+    assert err[128] < 5e-4
+    assert err[128] < 0.1 * err[32]
+
+
+def test_numerical_and_analytic_filters_agree_in_the_passband(circle_analytic):
+    # Fig. 1 / Sec. III-C: inside the disc (away from the pole at kappa = k) the numerically filtered
+    # spectrum approaches the analytic one as eps^2 (the zeroed self cell); beyond alpha the analytic
+    # spectrum keeps only the ringing of the finite window (Eq. 11's sinc), the numerical one is zero
+    N, nodes, G, ops = circle_analytic
+    diff = {}
+    for m in (32, 64, 128):
+        an, nu = ops[(m, "analytic")], ops[(m, "numerical")]
+        P = 2 * m
+        t = aim.signed_index(P)
+        kap = (2 * math.pi / (P * an.eps)) * np.hypot(t[:, None], t[None, :])
+        inside = (kap < 0.9 * 4 * K) & (np.abs(kap - K) > 0.3 * K)
+        outside = kap > 1.1 * 4 * K
+        diff[m] = np.linalg.norm((an.Chat_alpha - nu.Chat_alpha)[inside]) / np.linalg.norm(nu.Chat_alpha[inside])
+        assert np.all(nu.Chat_alpha[outside] == 0)
+        assert np.abs(an.Chat_alpha[outside]).max() < 0.03 * np.abs(nu.Chat_alpha[inside]).max()
+    assert diff[64] < diff[32] / 3 and diff[128] < diff[64] / 3
+    assert diff[128] < 0.02
+
+
+# --------------------------------------------------------------------------------------
 # Solvers
 # --------------------------------------------------------------------------------------
 def test_gmres_matches_dense_solve():
