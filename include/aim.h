@@ -301,6 +301,24 @@ aim_status aim_solve(aim_ctx* ctx, aim_op system, int nrhs, const void* rhs, voi
                      int x0_given, const aim_solve_opts* opts, aim_solve_info* info,
                      void* stream);
 
+/* Golub-Kahan-Lanczos bidiagonalisation of an operator, for the singular-value studies of
+ * Sec. IV (Figs. 2-3). k steps of
+ *     A v_j = alpha_j u_j + beta_{j-1} u_{j-1},   A^H u_j = alpha_j v_j + beta_j v_{j+1},
+ * started from v_0 = v0/||v0|| (n complex128, host or device; the caller supplies the start, for
+ * instance a seeded random vector), with both bases reorthogonalised in full (classical
+ * Gram-Schmidt twice, FP64) and every product A x, A^H x computed by the library's grid product in
+ * `precision`. The singular values of the k x k upper bidiagonal matrix with alpha_0..alpha_{k-1} on
+ * the diagonal and beta_0..beta_{k-2} above it approximate those of A, and equal them for k = n (up to
+ * rounding). alpha, beta: host arrays of k doubles (beta_{k-1} is the norm of the next residual).
+ * U (k x n) and V ((k+1) x n): device arrays that receive the Lanczos vectors u_j, v_j row by row, or
+ * NULL. The adjoint uses the complex symmetry of the TE Galerkin operators: op is AIM_OP_S, S_ALPHA,
+ * N, N_ALPHA, GRAM_INV, EFIE or one of the Calderon products (transposed as the reversed chain
+ * N G^-1 S G^-1). Errors: AIM_EINVAL (k < 1 or k > n, another operator, U/V not device memory),
+ * AIM_ESTATE (TM context: collocation operators are not symmetric), AIM_ENUMERIC, AIM_ENOMEM,
+ * AIM_ECUDA. Synchronises `stream`. */
+aim_status aim_lanczos_bidiag(aim_ctx* ctx, aim_op op, int k, int precision, const void* v0,
+                              double* alpha, double* beta, void* U, void* V, void* stream);
+
 /* Device bytes that aim_setup followed by aim_reserve(nrhs, precision) would hold at their
  * peak, without touching the GPU (admission control; no counterpart in the paper). The count
  * runs the host part of the setup (grid, projections of Eq. 7 and the near-field pattern for

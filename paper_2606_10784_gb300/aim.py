@@ -133,6 +133,8 @@ def lib() -> ctypes.CDLL:
     L.aim_query_solve_bytes.restype = i
     L.aim_grid_product_noalloc.argtypes = [vp, i, i, vp, vp, i, vp]
     L.aim_grid_product_noalloc.restype = i
+    L.aim_lanczos_bidiag.argtypes = [vp, i, i, i, vp, ctypes.POINTER(d), ctypes.POINTER(d), vp, vp, vp]
+    L.aim_lanczos_bidiag.restype = i
     L.aim_kernel_table.argtypes = [vp, i, vp, vp]
     L.aim_kernel_table.restype = i
     L.aim_autotune.argtypes = [vp, i, i, vp, ctypes.POINTER(Schedule)]
@@ -282,6 +284,18 @@ class Context:
         """(H+1) x (H+1) grid kernel table (aim_kernel_table): spectra or analytic samples."""
         _check(lib().aim_kernel_table(self._h, int(which), _ptr(out), _stream_ptr(stream)), "aim_kernel_table")
         return out
+
+    def lanczos_bidiag(self, op, k: int, v0, precision: int = FP64, U=None, V=None, stream=None):
+        """k Golub-Kahan-Lanczos steps from v0 (aim_lanczos_bidiag): returns (alpha, beta) as numpy arrays."""
+        op = OPS[op] if isinstance(op, str) else int(op)
+        alpha = np.zeros(int(k), dtype=np.float64)
+        beta = np.zeros(int(k), dtype=np.float64)
+        _check(lib().aim_lanczos_bidiag(self._h, op, int(k), int(precision), _ptr(v0),
+                                        alpha.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        beta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                        _ptr(U) if U is not None else None, _ptr(V) if V is not None else None,
+                                        _stream_ptr(stream)), "aim_lanczos_bidiag")
+        return alpha, beta
 
     def rhs_planewave(self, angles, out, stream=None):
         ang = np.ascontiguousarray(np.asarray(angles, dtype=np.float64).reshape(-1))

@@ -45,3 +45,4 @@ def test_unknown_policy_is_refused():
     from paper_2606_10784_gb300 import serving
     with pytest.raises(ValueError):
         serving.Server(1 << 20, policy="lifo")
+
