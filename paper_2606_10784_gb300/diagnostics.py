@@ -65,9 +65,14 @@ def lanczos_svd(ctx: aim.Context, op: str, n: int, k: int | None = None, precisi
         return np.linalg.svd(B, compute_uv=False)
     _, s, Wh = np.linalg.svd(B)
     # A V_k = U_k B and B = Y diag(s) W^H: the right singular vectors of A are V_k W
-    W = torch.from_numpy(np.ascontiguousarray(Wh.conj().T)).cuda()
+    W = torch.from_numpy(np.ascontiguousarray(Wh.conj().T).astype(np.complex128)).cuda()
     vecs = (V[:k].transpose(0, 1) @ W).cpu().numpy()
     return s, vecs
+
+
+def singular_values(ctx: aim.Context, op: str, n: int, precision: int = aim.FP64, seed: int = 0) -> np.ndarray:
+    """All n singular values of `op`, largest first (n Lanczos steps)."""
+    return lanczos_svd(ctx, op, n, None, precision, seed)
 
 
 def laplace_beltrami(nodes: np.ndarray):
