@@ -237,6 +237,24 @@ aim_status aim_rhs_planewave(aim_ctx* ctx, int nrhs, const double* angles, void*
 aim_status aim_matvec(aim_ctx* ctx, aim_op op, int nrhs, const void* x, void* y,
                       int precision, void* stream);
 
+/* y_i = A_i x_i for `count` (1..32) contexts of any sizes at once (no counterpart in the paper; a
+ * batching of Eq. 8 / Eq. 10 across problems). Every grid pass stage of all the contexts - the
+ * forward row passes with anterpolation, the column passes, the inverse row passes and the
+ * gathers with their near-field rows - runs in ONE persistent cooperative launch whose CTAs take
+ * work items (context, channel, group of rows or columns) from all of them; the Calderon products
+ * take two such launches with the Gram inverses between them (Eq. 3). The launch separates its
+ * phases by grid barriers whose waits are bounded (AIM_ETIMEOUT if one gives up). Each result is
+ * bit-identical to aim_matvec on that context alone with the same schedule. ctxs, ops, nrhs, x,
+ * y: host arrays of `count` entries; x[i], y[i]: device pointers to nrhs[i] vectors of context i;
+ * a context appears at most once. All contexts must be current on this device and share the pass
+ * geometry (transforms and elements per thread) of their schedule in `precision` (otherwise
+ * AIM_EINVAL). One launch serves contexts whose transforms fit one CTA size (a CTA takes
+ * max(2, 32-byte tile) lines of the longest transform and correspondingly more lines of shorter
+ * ones, at most a context's P); a stage whose contexts span more than that (for example P = 64
+ * beside P = 2048) is split into the fewest such launches. Synchronises `stream`. */
+aim_status aim_matvec_multi(int count, aim_ctx* const* ctxs, const aim_op* ops, const int* nrhs,
+                            const void* const* x, void* const* y, int precision, void* stream);
+
 /* The grid product alone (the bracket of Eq. 8, or of Eq. 10 when filtered != 0) on
  * full m x m grids: v = [F^-1(F(c) .* F(b))]_restr with b = u zero-padded to P x P.
  * u and v hold nrhs row-major m x m complex128 grids (element (iy, ix) at iy*m + ix);

@@ -133,6 +133,9 @@ def lib() -> ctypes.CDLL:
     L.aim_query_solve_bytes.restype = i
     L.aim_grid_product_noalloc.argtypes = [vp, i, i, vp, vp, i, vp]
     L.aim_grid_product_noalloc.restype = i
+    L.aim_matvec_multi.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(vp),
+                                   ctypes.POINTER(vp), i, vp]
+    L.aim_matvec_multi.restype = i
     L.aim_lanczos_bidiag.argtypes = [vp, i, i, i, vp, ctypes.POINTER(d), ctypes.POINTER(d), vp, vp, vp]
     L.aim_lanczos_bidiag.restype = i
     L.aim_kernel_table.argtypes = [vp, i, vp, vp]
@@ -155,6 +158,20 @@ def lib() -> ctypes.CDLL:
     L.aim_last_error.restype = ctypes.c_char_p
     _lib = L
     return L
+
+
+def matvec_multi(ctxs, ops, xs, ys, precision: int = FP64, stream=None):
+    """y_i = A_i x_i for several contexts (of any sizes) in one persistent launch per grid-pass stage
+    (aim_matvec_multi); xs, ys: device tensors of shape (nrhs_i, n_i)."""
+    count = len(ctxs)
+    arr_c = (ctypes.c_void_p * count)(*[c._h.value for c in ctxs])
+    arr_o = (ctypes.c_int * count)(*[OPS[o] if isinstance(o, str) else int(o) for o in ops])
+    arr_r = (ctypes.c_int * count)(*[x.shape[0] if x.ndim == 2 else 1 for x in xs])
+    arr_x = (ctypes.c_void_p * count)(*[_ptr(x) for x in xs])
+    arr_y = (ctypes.c_void_p * count)(*[_ptr(y) for y in ys])
+    _check(lib().aim_matvec_multi(count, arr_c, arr_o, arr_r, arr_x, arr_y, int(precision), _stream_ptr(stream)),
+           "aim_matvec_multi")
+    return ys
 
 
 class AimError(RuntimeError):

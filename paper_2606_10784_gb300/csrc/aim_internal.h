@@ -46,7 +46,7 @@ aim_status check_device(const aim_ctx* ctx);
 enum KernelId {
   K_ROW_FWD = 0, K_COL_CONV, K_ROW_INV, K_GATHER, K_GRAM,
   K_SETUP_SAMPLE, K_SETUP_DFT, K_SETUP_PACK, K_SETUP_SEGPAIRS, K_SETUP_NEAR,
-  K_RHS, K_GMRES, K_COUNT
+  K_RHS, K_GMRES, K_MULTI, K_COUNT
 };
 void count_launches(int id, int n);   // counted, not timed
 void thread_launch_counts(long long* out);   // this host thread's counts, K_COUNT entries
@@ -251,10 +251,35 @@ aim_status grid_product_dense(aim_ctx* ctx, bool filtered, int nrhs, const doubl
 aim_status gram_inv_apply(aim_ctx* ctx, int nrhs, const double2* x, double2* y, cudaStream_t st);
 size_t inter_bytes_needed(const aim_ctx* ctx, int channels, int precision);
 
+// several grid passes of several contexts in one persistent launch (matvec_kernels.cuh)
+struct MultiPassSpec {   // one pass of a multi launch, as the caller describes it
+  aim_ctx* ctx;
+  PassSpec spec;
+  int nrhs;
+  const double2* x;
+  double2* y;
+};
+template <typename T>
+aim_status grid_pass_multi(const MultiPassSpec* passes, int count, unsigned* scratch, int* err_host, cudaStream_t st);
+
 // full operator application with composition (capi.cu)
 aim_status apply_op(aim_ctx* ctx, aim_op op, int nrhs, const double2* x, double2* y, int precision,
                     cudaStream_t st);
 aim_status reserve(aim_ctx* ctx, int nrhs, int precision);
+
+// Buffers of a multi-context launch: the barrier words and the error flags of its stages
+// (pinned). Owned by one caller at a time.
+struct MultiLauncher {
+  unsigned* scratch = nullptr;   // 4 words per stage
+  int* err_host = nullptr;       // one flag per stage (pinned)
+  aim_status init();
+  aim_status check();            // after a synchronisation: AIM_ETIMEOUT if a launch gave up
+  ~MultiLauncher();
+};
+// y_i = A_i x_i for `count` contexts (device vectors), every grid pass stage of all of them in one
+// persistent launch; composite operators run stage by stage (Eq. 3). Asynchronous on `st`.
+aim_status apply_op_multi(MultiLauncher& ml, int count, aim_ctx* const* ctxs, const aim_op* ops, const int* nrhs,
+                          const double2* const* x, double2* const* y, int precision, cudaStream_t st);
 
 // ------------------------------------------------------------------------------------
 // GMRES (solver.cu)

@@ -204,6 +204,104 @@ aim_status apply_op(aim_ctx* ctx, aim_op op, int nrhs, const double2* x, double2
 
 aim_status device_spectra_and_near(aim_ctx* ctx, const HostSetup& hs, cudaStream_t st);
 
+// ------------------------------------------------------------------------------------
+// several contexts per launch
+// ------------------------------------------------------------------------------------
+constexpr int kMultiStages = 2;
+
+aim_status MultiLauncher::init() {
+  if (scratch != nullptr) return AIM_OK;
+  void* p = nullptr;
+  AIM_CUDA_TRY(cudaMalloc(&p, kMultiStages * 4 * sizeof(unsigned)));
+  scratch = static_cast<unsigned*>(p);
+  AIM_CUDA_TRY(cudaMallocHost(&p, kMultiStages * sizeof(int)));
+  err_host = static_cast<int*>(p);
+  for (int i = 0; i < kMultiStages; ++i) err_host[i] = 0;
+  return AIM_OK;
+}
+
+aim_status MultiLauncher::check() {
+  for (int i = 0; i < kMultiStages; ++i)
+    if (err_host != nullptr && err_host[i] != 0) {
+      err_host[i] = 0;
+      return fail(AIM_ETIMEOUT, "a grid barrier of the multi-context launch gave up waiting");
+    }
+  return AIM_OK;
+}
+
+MultiLauncher::~MultiLauncher() {
+  if (scratch) cudaFree(scratch);
+  if (err_host) cudaFreeHost(err_host);
+}
+
+static aim_status multi_stage(MultiLauncher& ml, int stage, const std::vector<MultiPassSpec>& passes, int precision,
+                              cudaStream_t st) {
+  if (passes.empty()) return AIM_OK;
+  unsigned* sc = ml.scratch + 4 * stage;
+  int* eh = ml.err_host + stage;
+  if (precision == AIM_MIXED) return grid_pass_multi<float2>(passes.data(), (int)passes.size(), sc, eh, st);
+  if (precision == AIM_FP64_NATIVE) return grid_pass_multi<double2>(passes.data(), (int)passes.size(), sc, eh, st);
+  return grid_pass_multi<dfc>(passes.data(), (int)passes.size(), sc, eh, st);
+}
+
+aim_status apply_op_multi(MultiLauncher& ml, int count, aim_ctx* const* ctxs, const aim_op* ops, const int* nrhs,
+                          const double2* const* x, double2* const* y, int precision, cudaStream_t st) {
+  AIM_TRY(ml.init());
+  std::vector<MultiPassSpec> first, second;
+  for (int i = 0; i < count; ++i) {
+    aim_ctx* ctx = ctxs[i];
+    const bool te = ctx->form == AIM_TE_P1_GALERKIN;
+    if (ctx->reserved_rhs[precision] < nrhs[i]) AIM_TRY(reserve(ctx, nrhs[i], precision));
+    const aim_op op = ops[i];
+    switch (op) {
+      case AIM_OP_S: case AIM_OP_S_ALPHA:
+        first.push_back({ctx, make_spec(ctx, op), nrhs[i], x[i], y[i]});
+        break;
+      case AIM_OP_N: case AIM_OP_N_ALPHA:
+        if (!te) return fail(AIM_ESTATE, "N is a TE operator");
+        first.push_back({ctx, make_spec(ctx, op), nrhs[i], x[i], y[i]});
+        break;
+      case AIM_OP_EFIE:
+        first.push_back({ctx, make_spec(ctx, te ? AIM_OP_N : AIM_OP_EFIE), nrhs[i], x[i], y[i]});
+        break;
+      case AIM_OP_EFIE_ALPHA:
+        if (te) return fail(AIM_ESTATE, "the filtered EFIE system is defined for TM contexts");
+        first.push_back({ctx, make_spec(ctx, op), nrhs[i], x[i], y[i]});
+        break;
+      case AIM_OP_GRAM_INV:
+        if (!te) return fail(AIM_ESTATE, "G is a TE operator");
+        break;
+      case AIM_OP_CALDERON: case AIM_OP_CALDERON_ALPHA: case AIM_OP_CALDERON_ALPHA2: {
+        if (!te) return fail(AIM_ESTATE, "the Calderon product is a TE operator");
+        double2* t1 = ctx->vec_ws;
+        double2* t2 = ctx->vec_ws + (size_t)nrhs[i] * ctx->n;
+        first.push_back({ctx, make_spec(ctx, op == AIM_OP_CALDERON_ALPHA2 ? AIM_OP_N_ALPHA : AIM_OP_N), nrhs[i], x[i], t1});
+        second.push_back({ctx, make_spec(ctx, op == AIM_OP_CALDERON ? AIM_OP_S : AIM_OP_S_ALPHA), nrhs[i], t2, t1});
+        break;
+      }
+      default:
+        return fail(AIM_EINVAL, "unknown operator");
+    }
+  }
+  // stage 1: every context's first grid pass, then the Gram inverses between the Calderon factors
+  AIM_TRY(multi_stage(ml, 0, first, precision, st));
+  for (int i = 0; i < count; ++i) {
+    aim_ctx* ctx = ctxs[i];
+    const aim_op op = ops[i];
+    if (op == AIM_OP_GRAM_INV) AIM_TRY(gram_inv_apply(ctx, nrhs[i], x[i], y[i], st));
+    if (op == AIM_OP_CALDERON || op == AIM_OP_CALDERON_ALPHA || op == AIM_OP_CALDERON_ALPHA2)
+      AIM_TRY(gram_inv_apply(ctx, nrhs[i], ctx->vec_ws, ctx->vec_ws + (size_t)nrhs[i] * ctx->n, st));
+  }
+  // stage 2: the single-layer factors of the Calderon products, then their last Gram inverse
+  AIM_TRY(multi_stage(ml, 1, second, precision, st));
+  for (int i = 0; i < count; ++i) {
+    const aim_op op = ops[i];
+    if (op == AIM_OP_CALDERON || op == AIM_OP_CALDERON_ALPHA || op == AIM_OP_CALDERON_ALPHA2)
+      AIM_TRY(gram_inv_apply(ctxs[i], nrhs[i], ctxs[i]->vec_ws, y[i], st));
+  }
+  return AIM_OK;
+}
+
 }  // namespace aim
 
 using namespace aim;
@@ -521,6 +619,28 @@ aim_status aim_matvec(aim_ctx* ctx, aim_op op, int nrhs, const void* x, void* y,
     AIM_CUDA_TRY(cudaStreamSynchronize(st));
   }
   return AIM_OK;
+}
+
+aim_status aim_matvec_multi(int count, aim_ctx* const* ctxs, const aim_op* ops, const int* nrhs, const void* const* x,
+                            void* const* y, int precision, void* stream) {
+  if (count < 1 || count > 32 || !ctxs || !ops || !nrhs || !x || !y) return fail(AIM_EINVAL, "bad argument");
+  if (precision < AIM_FP64 || precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "precision must be 0, 1 or 2");
+  for (int i = 0; i < count; ++i) {
+    if (!ctxs[i] || nrhs[i] < 1 || !x[i] || !y[i]) return fail(AIM_EINVAL, "bad argument");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return fail(AIM_EINVAL, "a context may appear once per multi-context call");
+    if (x[i] == y[i]) return fail(AIM_EINVAL, "x and y must not overlap");
+    if (!device_pointer(x[i]) || !device_pointer(y[i])) return fail(AIM_EINVAL, "x and y must be device pointers");
+    AIM_TRY(check_device(ctxs[i]));
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  MultiLauncher ml;
+  aim_status s = apply_op_multi(ml, count, ctxs, ops, nrhs, reinterpret_cast<const double2* const*>(x),
+                                reinterpret_cast<double2* const*>(y), precision, st);
+  const cudaError_t e = cudaStreamSynchronize(st);
+  if (s == AIM_OK && e != cudaSuccess) s = fail(AIM_ECUDA, std::string("multi-context product: ") + cudaGetErrorString(e));
+  if (s == AIM_OK) s = ml.check();
+  return s;
 }
 
 aim_status aim_grid_product(aim_ctx* ctx, int filtered, int nrhs, const void* u, void* v, int precision, void* stream) {

@@ -7,5 +7,6 @@ namespace aim {
 template aim_status grid_pass<dfc>(aim_ctx*, const PassSpec&, int, const double2*, double2*, cudaStream_t);
 template aim_status grid_product_dense<dfc>(aim_ctx*, bool, int, const double2*, double2*, void*, size_t,
                                           cudaStream_t);
+template aim_status grid_pass_multi<dfc>(const MultiPassSpec*, int, unsigned*, int*, cudaStream_t);
 
 }  // namespace aim

@@ -7,5 +7,6 @@ namespace aim {
 template aim_status grid_pass<double2>(aim_ctx*, const PassSpec&, int, const double2*, double2*, cudaStream_t);
 template aim_status grid_product_dense<double2>(aim_ctx*, bool, int, const double2*, double2*, void*, size_t,
                                           cudaStream_t);
+template aim_status grid_pass_multi<double2>(const MultiPassSpec*, int, unsigned*, int*, cudaStream_t);
 
 }  // namespace aim

@@ -30,7 +30,9 @@
 // row passes touch whole 32-byte sectors. Only grid rows that hold active points are stored.
 #pragma once
 
+#include <algorithm>
 #include <type_traits>
+#include <vector>
 
 #include "aim_internal.h"
 #include "gridtypes.cuh"
@@ -58,18 +60,18 @@ struct RowFwdArgs {
 // CTA: rows_per_cta rows of one channel; (3 - TPT) * H/E threads per row (E = 2^LOGE elements each).
 constexpr int kAntChunk = 8;
 
+// One work item of the forward row pass: rows [row_block * rows_per_cta, +rows_per_cta) of channel c.
+// Every thread of the CTA calls it (it holds barriers); `smraw` is the CTA's dynamic shared memory.
 template <typename CT, int TPT, int LOGE>
-__global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_fwd(RowFwdArgs a) {
+__device__ __forceinline__ void row_fwd_item(const RowFwdArgs& a, int row_block, int c, unsigned char* smraw) {
   using T2 = CT;
   constexpr int W = GridT<CT>::W, NF = TPT, LPT = 3 - TPT;
-  extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
   const int H = 1 << a.logH, P = 1 << a.logP, tpf = H >> LOGE, HS = padded_len<LOGE>(H);
   const int per_row = LPT * tpf;
   const int g = threadIdx.x / per_row, rem = threadIdx.x - g * per_row;
   const int half = TPT == 1 ? (rem & 1) : 0, j = TPT == 1 ? (rem >> 1) : rem;
-  const int rloc = blockIdx.x * a.rows_per_cta + g;
-  const int c = blockIdx.y;
+  const int rloc = row_block * a.rows_per_cta + g;
   const bool live = rloc < a.nrows;
   const int iy = a.row_lo + rloc;
   const T2* tw = static_cast<const T2*>(a.tw);
@@ -170,6 +172,12 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_fwd(Row
   });
 }
 
+template <typename CT, int TPT, int LOGE>
+__global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_fwd(RowFwdArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  row_fwd_item<CT, TPT, LOGE>(a, blockIdx.x, blockIdx.y, smraw);
+}
+
 // ------------------------------------------------------------------------------------
 // column pass: forward DFT x spectrum x inverse DFT
 // ------------------------------------------------------------------------------------
@@ -200,11 +208,11 @@ __device__ __forceinline__ T2 recombine(const T2 (&v)[TPT], int half, const T2* 
 // adjacent lanes (lane pairs when TPT = 1), so with a whole tile per CTA the global loads and
 // stores of a warp are whole 32-byte sectors; with fewer columns per CTA the CTAs of the
 // neighbouring columns read the rest of each sector, through L2.
+// One work item of the column pass: column tile `ctile` (2^log_cols columns) of channel c.
 template <typename CT, int TPT, int LOGE>
-__global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_col_conv(ColArgs a) {
+__device__ __forceinline__ void col_conv_item(const ColArgs& a, int ctile, int c, unsigned char* smraw) {
   using T2 = CT;
   constexpr int W = GridT<CT>::W, NF = TPT, LPT = 3 - TPT;
-  extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
   const int H = 1 << a.logH, P = 1 << a.logP, tpf = H >> LOGE, HS = padded_len<LOGE>(H);
   const int cw = min(1 << a.log_cols, W);               // columns side by side in the lanes
@@ -214,13 +222,8 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_col_conv(Co
   const int r2 = TPT == 1 ? (rem >> 1) : rem;
   const int wl = r2 & (cw - 1), j = r2 / cw;
   const int colc = g * cw + wl;                         // column within the CTA
-  // with many channels they run along x: the channels of one column tile run back to back and
-  // share its spectrum column through L2 (64 right-hand sides: 2.82 -> 2.67 ms per launch);
-  // with few, column tiles run along x (no gain measured for 3 channels)
-  const int ctile = a.chan_x ? blockIdx.y : blockIdx.x;
   const int qcol = (ctile << a.log_cols) + colc;   // column of the grid
   const int w = qcol & (W - 1), tile = qcol / W;
-  const int c = a.chan_x ? blockIdx.x : blockIdx.y;
   if (a.live != nullptr) {
     // the filtered spectrum (Eq. 10) vanishes on columns beyond the mask radius: when it does on
     // every column of this CTA their product is zero, so write zeros and skip the transforms
@@ -292,6 +295,15 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_col_conv(Co
   });
 }
 
+template <typename CT, int TPT, int LOGE>
+__global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_col_conv(ColArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  // with many channels they run along x: the channels of one column tile run back to back and
+  // share its spectrum column through L2 (64 right-hand sides: 2.82 -> 2.67 ms per launch);
+  // with few, column tiles run along x (no gain measured for 3 channels)
+  col_conv_item<CT, TPT, LOGE>(a, a.chan_x ? blockIdx.y : blockIdx.x, a.chan_x ? blockIdx.x : blockIdx.y, smraw);
+}
+
 // ------------------------------------------------------------------------------------
 // row pass, inverse + restriction
 // ------------------------------------------------------------------------------------
@@ -309,19 +321,18 @@ struct RowInvArgs {
   int rows_per_cta;
 };
 
+// One work item of the inverse row pass: rows [row_block * rows_per_cta, +rows_per_cta) of channel c.
 template <typename CT, int TPT, int LOGE>
-__global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_inv(RowInvArgs a) {
+__device__ __forceinline__ void row_inv_item(const RowInvArgs& a, int row_block, int c, unsigned char* smraw) {
   using T2 = CT;
   using VT = typename GridT<CT>::VT;
   constexpr int W = GridT<CT>::W, NF = TPT, LPT = 3 - TPT;
-  extern __shared__ __align__(16) unsigned char smraw[];
   T2* sm = reinterpret_cast<T2*>(smraw);
   const int H = 1 << a.logH, P = 1 << a.logP, tpf = H >> LOGE, HS = padded_len<LOGE>(H);
   const int per_row = LPT * tpf;
   const int g = threadIdx.x / per_row, rem = threadIdx.x - g * per_row;
   const int half = TPT == 1 ? (rem & 1) : 0, j = TPT == 1 ? (rem >> 1) : rem;
-  const int rloc = blockIdx.x * a.rows_per_cta + g;
-  const int c = blockIdx.y;
+  const int rloc = row_block * a.rows_per_cta + g;
   const bool live = rloc < a.nrows;
   const int iy = a.row_lo + rloc;
   const T2* tw = static_cast<const T2*>(a.tw);
@@ -378,6 +389,12 @@ __global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_inv(Row
   }
 }
 
+template <typename CT, int TPT, int LOGE>
+__global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_row_inv(RowInvArgs a) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  row_inv_item<CT, TPT, LOGE>(a, blockIdx.x, blockIdx.y, smraw);
+}
+
 // ------------------------------------------------------------------------------------
 // gather + near field, Gram inverse
 // ------------------------------------------------------------------------------------
@@ -410,11 +427,13 @@ struct GatherArgs {
 // near-field rows and the sums over projections stay in FP64.
 constexpr int kGatherLanes = 8;
 
+// Gather for the threads of virtual block `vblock` (blockDim.x threads each); all 32 lanes of every
+// warp call it (the group sums are shuffles).
 template <typename T2, int kGatherRhs>
-__global__ void k_gather(GatherArgs a) {
+__device__ __forceinline__ void gather_item(const GatherArgs& a, long long vblock) {
   static_assert(kGatherRhs <= kGatherLanes, "lane g writes right-hand side r0 + g");
   using Acc = typename std::conditional<std::is_same<T2, float2>::value, float, double>::type;
-  const long long grp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / kGatherLanes;
+  const long long grp = (vblock * blockDim.x + threadIdx.x) / kGatherLanes;
   const int g = threadIdx.x & (kGatherLanes - 1);
   const int nblk = (a.nrhs + kGatherRhs - 1) / kGatherRhs;
   const bool valid = grp < (long long)a.n * nblk;
@@ -493,6 +512,11 @@ __global__ void k_gather(GatherArgs a) {
     }
     *dst = o;
   }
+}
+
+template <typename T2, int kGatherRhs>
+__global__ void k_gather(GatherArgs a) {
+  gather_item<T2, kGatherRhs>(a, blockIdx.x);
 }
 
 // ------------------------------------------------------------------------------------
@@ -735,6 +759,316 @@ aim_status grid_pass(aim_ctx* ctx, const PassSpec& spec, int nrhs, const double2
   AIM_CUDA_TRY(cudaGetLastError());
   return AIM_OK;
 }
+
+// ------------------------------------------------------------------------------------
+// several grid passes (contexts of any size) in one persistent launch
+// ------------------------------------------------------------------------------------
+// One job is a whole grid pass of one context (its channels, its spectrum, its gather). The
+// persistent kernel runs four phases over all jobs' work items: forward row pass, column pass,
+// inverse row pass, gather. Every CTA takes items c, c + G, c + 2G, ... of the flattened item list
+// of a phase (G = CTAs of the launch); each item fills the CTA's threads with lines (rows or
+// columns) of its job, so a job with a shorter transform puts more lines into one item. A grid
+// barrier separates the phases. The launch is cooperative, so all CTAs are resident and the
+// barrier completes; its waits are bounded all the same: after max_spins polls a CTA records the
+// failure in *err and every CTA leaves at its next barrier, and the host reports AIM_ETIMEOUT.
+constexpr int kMaxMultiJobs = 32;
+
+struct MultiJob {
+  RowFwdArgs fa;
+  ColArgs ca;
+  RowInvArgs ia;
+  GatherArgs ga;
+  int row_items;       // row blocks per channel
+  int col_items;       // column tiles per channel
+  int channels;
+  int tile_major;      // column items ordered tile by tile (the channels of a tile adjacent)
+  int gather_rb;       // right-hand sides per gather group (1 or 8)
+};
+
+// The whole job table travels as the kernel's parameter (read-only, in the constant bank: a
+// uniform load per field, as for the single-context kernels' arguments).
+struct MultiArgs {
+  MultiJob jobs[kMaxMultiJobs];
+  int njobs;
+  long long off[4][kMaxMultiJobs + 1];   // prefix sums of the items of each phase over the jobs
+  unsigned* bar;                         // [arrivals, generation], zero at launch
+  int* err;                              // 1 when a barrier wait gave up
+  long long max_spins;
+};
+
+static_assert(sizeof(MultiArgs) <= 32000, "the job table must fit the kernel parameter space (32 KB)");
+
+__device__ __forceinline__ bool multi_grid_barrier(const MultiArgs& m) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = m.bar + 1;
+    volatile int* err = m.err;
+    const unsigned g0 = *gen;
+    __threadfence();
+    if (atomicAdd(m.bar, 1u) == gridDim.x - 1) {
+      atomicExch(m.bar, 0u);
+      __threadfence();
+      atomicAdd(m.bar + 1, 1u);
+    } else {
+      long long spins = 0;
+      while (*gen == g0) {
+        if (*err != 0) break;
+        if (++spins > m.max_spins) {
+          atomicExch(m.err, 1);
+          break;
+        }
+        __nanosleep(128);
+      }
+    }
+    __threadfence();
+    ok = *err == 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <typename CT, int TPT, int LOGE>
+__global__ void __launch_bounds__(LaunchMax<CT, TPT, LOGE>::value) k_grid_multi(const __grid_constant__ MultiArgs m) {
+  using VT = typename GridT<CT>::VT;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  for (int phase = 0; phase < 4; ++phase) {
+    const long long total = m.off[phase][m.njobs];
+    for (long long it = blockIdx.x; it < total; it += gridDim.x) {
+      int jb = 0;
+      while (it >= m.off[phase][jb + 1]) ++jb;   // the same job in every thread of the CTA
+      const MultiJob& J = m.jobs[jb];
+      const long long local = it - m.off[phase][jb];
+      if (phase == 0) {
+        row_fwd_item<CT, TPT, LOGE>(J.fa, (int)(local % J.row_items), (int)(local / J.row_items), smraw);
+      } else if (phase == 1) {
+        // many channels (right-hand sides): the channels of one column tile run back to back and
+        // share its spectrum column through L2, as the single-context launch orders them
+        const int tile = J.tile_major ? (int)(local / J.channels) : (int)(local % J.col_items);
+        const int ch = J.tile_major ? (int)(local % J.channels) : (int)(local / J.col_items);
+        col_conv_item<CT, TPT, LOGE>(J.ca, tile, ch, smraw);
+      } else if (phase == 2) {
+        row_inv_item<CT, TPT, LOGE>(J.ia, (int)(local % J.row_items), (int)(local / J.row_items), smraw);
+      } else if (J.gather_rb == 1) {
+        gather_item<VT, 1>(J.ga, local);
+      } else {
+        gather_item<VT, 8>(J.ga, local);
+      }
+      __syncthreads();   // the next item reuses the shared memory
+    }
+    if (phase < 3 && !multi_grid_barrier(m)) return;
+  }
+}
+
+// Runs the passes (all of element type CT, all contexts on the schedule geometry of jobs[0]: the
+// same transforms per thread and elements per thread) in one persistent cooperative launch.
+// scratch: 16 device bytes for the barrier and the error flag (zeroed here on the stream);
+// err_host: pinned host int that receives the error flag after the launch (read it after a sync).
+template <typename CT>
+aim_status grid_pass_multi(const MultiPassSpec* passes, int count, unsigned* scratch, int* err_host, cudaStream_t st);
+
+// Threads per CTA of a multi launch whose longest transform has half-length H: two lines of it and
+// at least a whole 32-byte column tile of it (W columns), at least a warp, within the launch bound.
+template <typename CT, int TPT, int LOGE>
+static int multi_cta_threads(int H) {
+  constexpr int LPT = 3 - TPT, W = GridT<CT>::W;
+  constexpr int Lmax = LaunchMax<CT, TPT, LOGE>::value;
+  int B = 32;
+  while (B < std::max(2, W) * LPT * (H >> LOGE) && B < Lmax) B *= 2;
+  return B;
+}
+
+// Whether a context with half-length H can share a launch of B threads per CTA: a CTA takes
+// B / (threads per line) of its lines, a power of two of at least one and at most its P columns.
+template <typename CT, int TPT, int LOGE>
+static bool multi_fits(int B, int H) {
+  constexpr int LPT = 3 - TPT;
+  const int per_line = LPT * (H >> LOGE);
+  return per_line >= 1 && B >= per_line && B / per_line <= 2 * H;
+}
+
+template <typename CT, int TPT, int LOGE>
+static aim_status launch_multi(const MultiPassSpec* passes, int count, unsigned* scratch, cudaStream_t st) {
+  using T2 = CT;
+  using VT = typename GridT<CT>::VT;
+  constexpr int LPT = 3 - TPT;
+  int maxH = 1;
+  for (int i = 0; i < count; ++i) maxH = std::max(maxH, passes[i].ctx->H);
+  const int B = multi_cta_threads<CT, TPT, LOGE>(maxH);
+  if (B < LPT * (maxH >> LOGE)) return fail(AIM_EINVAL, "transform too long for the multi-context launch");
+  static thread_local MultiArgs m;   // 17 KB: kept off the stack
+  m = MultiArgs{};
+  m.njobs = count;
+  m.bar = scratch;
+  m.err = reinterpret_cast<int*>(scratch + 2);
+  m.max_spins = 20000000;   // ~2.5 s of 128 ns polls
+  size_t smem = 0;
+  for (int i = 0; i < count; ++i) {
+    const MultiPassSpec& ps = passes[i];
+    aim_ctx* ctx = ps.ctx;
+    const PassSpec& spec = ps.spec;
+    const int H = ctx->H, P = ctx->P, tpf = H >> LOGE, HS = padded_len<LOGE>(H);
+    const int lines = B / (LPT * tpf);
+    if (!multi_fits<CT, TPT, LOGE>(B, H) || lines > P || (lines & (lines - 1)))
+      return fail(AIM_EINVAL, "contexts of too different sizes for one multi-context launch");
+    const int channels = spec.nproj * ps.nrhs;
+    const int precision = precision_of((CT*)nullptr);
+    if (inter_bytes_needed(ctx, channels, precision) > ctx->inter_bytes ||
+        (size_t)channels * ctx->n_act * sizeof(VT) > ctx->vact_bytes)
+      return fail(AIM_ESTATE, "grid workspace not reserved for this many right-hand sides");
+    smem = std::max(smem, 2 * (size_t)lines * HS * sizeof(T2));
+    MultiJob& J = m.jobs[i];
+    const void* tw = twiddles(ctx, (CT*)nullptr);
+    RowFwdArgs& fa = J.fa;
+    fa.x = ps.x;
+    fa.dense = 0;
+    fa.n = ctx->n;
+    fa.m = ctx->m;
+    fa.nrhs = ps.nrhs;
+    fa.row_ptr = ctx->row_ptr;
+    fa.act_ix = ctx->act_ix;
+    fa.sc_ptr = ctx->prj.sc_ptr;
+    fa.sc_col = ctx->prj.sc_col;
+    for (int pj = 0; pj < spec.nproj; ++pj) fa.w[pj] = ctx->prj.sc_w[spec.proj[pj]];
+    fa.inter = ctx->inter;
+    fa.tw = tw;
+    fa.logH = ctx->logH;
+    fa.logP = ctx->logP;
+    fa.row_lo = ctx->row_lo;
+    fa.nrows = ctx->nrows;
+    fa.rows_per_cta = lines;
+    ColArgs& ca = J.ca;
+    ca.inter = ctx->inter;
+    ca.spec = spectrum(ctx, spec.filtered, (CT*)nullptr);
+    ca.live = spec.filtered ? ctx->specA_live : nullptr;
+    ca.tw = tw;
+    ca.logH = ctx->logH;
+    ca.logP = ctx->logP;
+    ca.row_lo = ctx->row_lo;
+    ca.nrows = ctx->nrows;
+    int lc = 0;
+    while ((1 << lc) < lines) ++lc;
+    ca.log_cols = lc;
+    ca.chan_x = 0;
+    RowInvArgs& ia = J.ia;
+    ia.inter = ctx->inter;
+    ia.tw = tw;
+    ia.vact = ctx->vact;
+    ia.dense = 0;
+    ia.m = ctx->m;
+    ia.n_act = ctx->n_act;
+    ia.row_ptr = ctx->row_ptr;
+    ia.act_ix = ctx->act_ix;
+    ia.logH = ctx->logH;
+    ia.logP = ctx->logP;
+    ia.row_lo = ctx->row_lo;
+    ia.nrows = ctx->nrows;
+    ia.scale = 1.0 / ((double)P * (double)P);
+    ia.rows_per_cta = lines;
+    GatherArgs& ga = J.ga;
+    ga.vact = ctx->vact;
+    ga.n_act = ctx->n_act;
+    ga.n = ctx->n;
+    ga.nrhs = ps.nrhs;
+    ga.nproj = spec.nproj;
+    ga.ga_ptr = ctx->prj.ga_ptr;
+    ga.ga_act = ctx->prj.ga_act;
+    for (int pj = 0; pj < spec.nproj; ++pj) {
+      ga.w[pj] = ctx->prj.ga_w[spec.proj[pj]];
+      ga.coef[pj] = spec.coef[pj];
+    }
+    if (spec.near != nullptr && spec.near->nnz > 0) {
+      ga.nptr = spec.near->ptr;
+      ga.ncol = spec.near->col;
+      ga.nval = near_values(spec.near, spec.near_which, (CT*)nullptr);
+    }
+    ga.x = ps.x;
+    ga.out_scale = spec.out_scale;
+    ga.y = ps.y;
+    ga.accumulate = 0;
+    J.gather_rb = ps.nrhs == 1 ? 1 : 8;
+    J.row_items = (ctx->nrows + lines - 1) / lines;
+    J.col_items = P / lines;
+    J.channels = channels;
+    J.tile_major = channels >= 8;
+    const long long groups = (long long)ctx->n * ((ps.nrhs + J.gather_rb - 1) / J.gather_rb);
+    const long long gblocks = (groups * kGatherLanes + B - 1) / B;
+    m.off[0][i + 1] = m.off[0][i] + (long long)J.row_items * channels;
+    m.off[1][i + 1] = m.off[1][i] + (long long)J.col_items * channels;
+    m.off[2][i + 1] = m.off[2][i] + (long long)J.row_items * channels;
+    m.off[3][i + 1] = m.off[3][i] + gblocks;
+  }
+  if (smem > kMaxDynSmem) return fail(AIM_EINVAL, "multi-context launch needs too much shared memory");
+  auto kernel = k_grid_multi<CT, TPT, LOGE>;
+  AIM_TRY(ensure_smem(kernel, smem));
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  AIM_CUDA_TRY(cudaGetDevice(&dev));
+  AIM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  AIM_CUDA_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+  if (!coop) return fail(AIM_ECUDA, "device does not support cooperative launches");
+  AIM_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, B, smem));
+  if (per_sm < 1) return fail(AIM_EINVAL, "multi-context kernel does not fit an SM");
+  long long most = 0;
+  for (int ph = 0; ph < 4; ++ph) most = std::max(most, m.off[ph][count]);
+  const int grid = (int)std::max(1LL, std::min<long long>((long long)sms * per_sm, most));
+  AIM_CUDA_TRY(cudaMemsetAsync(scratch, 0, 2 * sizeof(unsigned), st));   // the barrier words (not the error flag)
+  {
+    // one launch: the three grid passes and the gathers of every job
+    ProfScope ps(K_MULTI, st);
+    void* params[] = {&m};
+    AIM_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(B), params, smem, st));
+  }
+  return AIM_OK;
+}
+
+// Splits the passes into the fewest launches whose contexts can share one CTA size (longest
+// transforms first; a context too short for the CTA size of a longer one goes to a later launch).
+template <typename CT, int TPT, int LOGE>
+static aim_status launch_multi_groups(const MultiPassSpec* passes, int count, unsigned* scratch, int* err_host,
+                                      cudaStream_t st) {
+  std::vector<int> left(count);
+  for (int i = 0; i < count; ++i) left[i] = i;
+  std::stable_sort(left.begin(), left.end(), [&](int a, int b) { return passes[a].ctx->H > passes[b].ctx->H; });
+  AIM_CUDA_TRY(cudaMemsetAsync(scratch + 2, 0, sizeof(int), st));   // the stage's error flag
+  std::vector<MultiPassSpec> group;
+  while (!left.empty()) {
+    const int B = multi_cta_threads<CT, TPT, LOGE>(passes[left[0]].ctx->H);
+    group.clear();
+    std::vector<int> rest;
+    for (int i : left) {
+      if (multi_fits<CT, TPT, LOGE>(B, passes[i].ctx->H)) group.push_back(passes[i]);
+      else rest.push_back(i);
+    }
+    const aim_status gs = launch_multi<CT, TPT, LOGE>(group.data(), (int)group.size(), scratch, st);
+    if (gs != AIM_OK) return gs;
+    left.swap(rest);
+  }
+  AIM_CUDA_TRY(cudaMemcpyAsync(err_host, scratch + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+  return AIM_OK;
+}
+
+template <typename CT>
+aim_status grid_pass_multi(const MultiPassSpec* passes, int count, unsigned* scratch, int* err_host, cudaStream_t st) {
+  if (count < 1 || count > kMaxMultiJobs) return fail(AIM_EINVAL, "1 to 32 passes per multi-context launch");
+  const int p = precision_of((CT*)nullptr);
+  const Schedule sc = passes[0].ctx->sched[p];
+  for (int i = 1; i < count; ++i) {
+    const Schedule& o = passes[i].ctx->sched[p];
+    if (o.tpt != sc.tpt || loge_of(o) != loge_of(sc))
+      return fail(AIM_EINVAL, "contexts of one multi-context launch must share the pass geometry of their schedule");
+  }
+  if constexpr (std::is_same<CT, double2>::value) {
+    return launch_multi_groups<CT, 2, 4>(passes, count, scratch, err_host, st);
+  } else {
+    if (loge_of(sc) == 3) {
+      if (sc.tpt == 1) return launch_multi_groups<CT, 1, 3>(passes, count, scratch, err_host, st);
+      return launch_multi_groups<CT, 2, 3>(passes, count, scratch, err_host, st);
+    }
+    if (sc.tpt == 1) return launch_multi_groups<CT, 1, 4>(passes, count, scratch, err_host, st);
+    return launch_multi_groups<CT, 2, 4>(passes, count, scratch, err_host, st);
+  }
+}
+
 
 template <typename CT>
 aim_status grid_product_dense(aim_ctx* ctx, bool filtered, int nrhs, const double2* u, double2* v, void* inter,

@@ -110,17 +110,16 @@ def lb_order(vecs: np.ndarray, lb_vecs: np.ndarray, G: np.ndarray) -> np.ndarray
 def spectrum_by_lb(ctx: aim.Context, op: str, nodes: np.ndarray, k: int | None = None, precision: int = aim.FP64,
                    seed: int = 0):
     """Fig. 2/3 data: singular values of `op` listed in the order of their matched Laplace-Beltrami
-    eigenvalues. Returns (lb_eigenvalue, lb_frequency, sigma), lb_frequency = sqrt(lam) * perimeter / (2 pi)
-    (the mode number |n| on a circle)."""
+    eigenvalues. Returns (lb_eigenvalue, lb_mode, sigma). lb_mode is the mode number of the matched
+    eigenvector: a closed curve's Laplace-Beltrami eigenvalues are 0 and then pairs (a cosine-like and
+    a sine-like mode), so eigenvector index i has mode number (i + 1) // 2, the |n| of e^{j n phi} on
+    a circle."""
     n = len(nodes)
     s, vecs = lanczos_svd(ctx, op, n, k, precision, seed, vectors=True)
     lam, X, G = laplace_beltrami(nodes)
     idx = lb_order(vecs, X, G)
-    order = np.argsort(lam[idx], kind="stable")
-    d = np.roll(np.asarray(nodes), -1, axis=0) - np.asarray(nodes)
-    perimeter = float(np.hypot(d[:, 0], d[:, 1]).sum())
-    lam_sorted = lam[idx][order]
-    return lam_sorted, np.sqrt(np.maximum(lam_sorted, 0.0)) * perimeter / (2 * math.pi), s[order]
+    order = np.argsort(idx, kind="stable")
+    return lam[idx][order], (idx[order] + 1) // 2, s[order]
 
 
 def knee(sv: np.ndarray, drop: float = 1e-3) -> int:
@@ -151,7 +150,7 @@ def main(argv=None):
     for op in dict.fromkeys([args.op, "S", "S_alpha"]):
         _, freq, s = spectrum_by_lb(ctx, op, nodes, args.k or None)
         out[op] = {"knee_1e-3": knee(s), "sv_head": [float(v) for v in s[:4]], "sv_tail": [float(v) for v in s[-4:]],
-                   "last_lb_frequency_above_1e-3": float(freq[s > 1e-3 * s.max()].max())}
+                   "last_lb_mode_above_1e-3": int(freq[s > 1e-3 * s.max()].max())}
     ctx.close()
     print(json.dumps(out))
 

