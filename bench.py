@@ -549,22 +549,33 @@ def serving_arm(args, aim=None):
                                          tol=SOLVE_TOL, restart=RESTART, arrival=s.t_arrival, rid=i))
     free, total = torch.cuda.mem_get_info()
     budget = int(0.6 * free)
-    srv = serving.Server(memory_budget_bytes=budget, slots=4, policy=args.policy)
-    serving.replay(srv, reqs[:n_warm])
-    l0 = aim.launch_count()
-    t0 = time.perf_counter()
-    res = serving.replay(srv, reqs[n_warm:])
-    el = time.perf_counter() - t0
-    srv.close()
-    timed = [r for r in res if r.rid >= n_warm]
-    summ = serving.latency_summary(timed)
+    import copy
+    runs = {}
+    for fused in (True, False):
+        rs = copy.deepcopy(reqs)
+        srv = serving.Server(memory_budget_bytes=budget, slots=4, policy=args.policy, fused=fused)
+        serving.replay(srv, rs[:n_warm])
+        l0 = aim.launch_count()
+        t0 = time.perf_counter()
+        res = serving.replay(srv, rs[n_warm:])
+        el = time.perf_counter() - t0
+        stats = srv.fusion_stats()
+        srv.close()
+        timed = [r for r in res if r.rid >= n_warm]
+        runs[fused] = {"latency": serving.latency_summary(timed), "wall_s": el, "refused": srv.refused,
+                       "gpu_launches": aim.launch_count() - l0, "fusion": stats}
+    summ = runs[True]["latency"]
     return {"metric": "served filtered Calderon solves: p50/p99 latency and solves/s", "value": summ.get("solves_per_s"),
             "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "dtype": precision, "data": "synthetic",
-            "latency": summ, "wall_s": el, "budget_bytes": budget, "refused": srv.refused,
-            "gpu_launches": aim.launch_count() - l0,
+            "latency": summ, "wall_s": runs[True]["wall_s"], "budget_bytes": budget, "refused": runs[True]["refused"],
+            "gpu_launches": runs[True]["gpu_launches"], "fusion": runs[True]["fusion"],
+            "unfused": {"latency": runs[False]["latency"], "wall_s": runs[False]["wall_s"],
+                        "gpu_launches": runs[False]["gpu_launches"]},
             "config": {"workload": "Poisson 200/s, perimeter log-U[5,500] wl, N=10/wl, grids 32^2..1024^2, "
                                    "1..16 rhs, %d timed requests after %d warm-up" % (len(reqs) - n_warm, n_warm),
-                       "policy": args.policy, "slots": 4}}
+                       "policy": args.policy, "slots": 4,
+                       "fusion": "the slots' solves share a batcher: products of concurrent requests of one size "
+                                 "class run in one multi-context launch per stage (unfused: each on its own)"}}
 
 
 # --------------------------------------------------------------------------------------

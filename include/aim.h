@@ -337,6 +337,29 @@ aim_status aim_solve(aim_ctx* ctx, aim_op system, int nrhs, const void* rhs, voi
 aim_status aim_lanczos_bidiag(aim_ctx* ctx, aim_op op, int k, int precision, const void* v0,
                               double* alpha, double* beta, void* U, void* V, void* stream);
 
+/* Fused products of concurrent solves (no counterpart in the paper; the batching side of serving).
+ * A batcher is shared by solves that run at the same time on different host threads, each on its
+ * own stream (aim_solve_batched). Their operator products become requests: requests of solves in
+ * one size class (P = 64-128 or 256-512; larger grids keep their own launches) are fused into
+ * one multi-context launch per grid-pass stage, as aim_matvec_multi does, on the batcher's own
+ * stream, ordered against each solve's stream by CUDA events (no host thread waits for the GPU). A
+ * request waits on the host until every solve of its class has submitted one, or max_wait_us. Each
+ * solve's result is bit-identical to aim_solve of that context alone. aim_batcher_create makes a
+ * batcher (its stream, events and launch buffers) on the current device; aim_batcher_destroy waits
+ * for its work and frees it (no solve may be using it). aim_batcher_stats: products requested,
+ * launches made, products that ran fused with others (host pointers, each may be NULL). */
+typedef struct aim_batcher aim_batcher;
+aim_status aim_batcher_create(int max_wait_us, aim_batcher** out);
+void aim_batcher_destroy(aim_batcher* batcher);
+aim_status aim_batcher_stats(aim_batcher* batcher, long long* products, long long* launches,
+                             long long* fused_products);
+/* aim_solve with its operator products going through `batcher` (see above); same arguments,
+ * results and errors, plus AIM_ETIMEOUT when a fused launch's grid barrier gave up. One batched
+ * solve per host thread at a time (AIM_ESTATE otherwise). */
+aim_status aim_solve_batched(aim_batcher* batcher, aim_ctx* ctx, aim_op system, int nrhs,
+                             const void* rhs, void* x, int x0_given, const aim_solve_opts* opts,
+                             aim_solve_info* info, void* stream);
+
 /* Device bytes that aim_setup followed by aim_reserve(nrhs, precision) would hold at their
  * peak, without touching the GPU (admission control; no counterpart in the paper). The count
  * runs the host part of the setup (grid, projections of Eq. 7 and the near-field pattern for

@@ -133,6 +133,15 @@ def lib() -> ctypes.CDLL:
     L.aim_query_solve_bytes.restype = i
     L.aim_grid_product_noalloc.argtypes = [vp, i, i, vp, vp, i, vp]
     L.aim_grid_product_noalloc.restype = i
+    L.aim_batcher_create.argtypes = [i, ctypes.POINTER(vp)]
+    L.aim_batcher_create.restype = i
+    L.aim_batcher_destroy.argtypes = [vp]
+    L.aim_batcher_destroy.restype = None
+    L.aim_batcher_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                    ctypes.POINTER(ctypes.c_longlong)]
+    L.aim_batcher_stats.restype = i
+    L.aim_solve_batched.argtypes = [vp, vp, i, i, vp, vp, i, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), vp]
+    L.aim_solve_batched.restype = i
     L.aim_matvec_multi.argtypes = [i, ctypes.POINTER(vp), ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(vp),
                                    ctypes.POINTER(vp), i, vp]
     L.aim_matvec_multi.restype = i
@@ -172,6 +181,32 @@ def matvec_multi(ctxs, ops, xs, ys, precision: int = FP64, stream=None):
     _check(lib().aim_matvec_multi(count, arr_c, arr_o, arr_r, arr_x, arr_y, int(precision), _stream_ptr(stream)),
            "aim_matvec_multi")
     return ys
+
+
+class Batcher:
+    """Fused operator products of solves that run at the same time on different threads
+    (aim_batcher_*); pass it to Context.solve(batcher=...)."""
+
+    def __init__(self, max_wait_us: int = 200):
+        h = ctypes.c_void_p()
+        _check(lib().aim_batcher_create(int(max_wait_us), ctypes.byref(h)), "aim_batcher_create")
+        self._h = h
+
+    def stats(self) -> dict:
+        p, l, f = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(lib().aim_batcher_stats(self._h, ctypes.byref(p), ctypes.byref(l), ctypes.byref(f)), "aim_batcher_stats")
+        return {"products": p.value, "launches": l.value, "fused_products": f.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().aim_batcher_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class AimError(RuntimeError):
@@ -341,13 +376,17 @@ class Context:
         return v
 
     def solve(self, system, rhs, x, tol=1e-8, restart=50, max_iter=1000, precision: int = FP64, inner_tol=0.0,
-              timeout_ms=0, x0_given=False, stream=None, check=True):
+              timeout_ms=0, x0_given=False, stream=None, check=True, batcher: Optional["Batcher"] = None):
         system = OPS[system] if isinstance(system, str) else int(system)
         nrhs = rhs.shape[0] if rhs.ndim == 2 else 1
         opts = SolveOpts(float(tol), int(restart), int(max_iter), int(precision), float(inner_tol), int(timeout_ms))
         infos = (SolveInfo * nrhs)()
-        st = lib().aim_solve(self._h, system, int(nrhs), _ptr(rhs), _ptr(x), int(bool(x0_given)), ctypes.byref(opts),
-                             infos, _stream_ptr(stream))
+        if batcher is not None:
+            st = lib().aim_solve_batched(batcher._h, self._h, system, int(nrhs), _ptr(rhs), _ptr(x), int(bool(x0_given)),
+                                         ctypes.byref(opts), infos, _stream_ptr(stream))
+        else:
+            st = lib().aim_solve(self._h, system, int(nrhs), _ptr(rhs), _ptr(x), int(bool(x0_given)),
+                                 ctypes.byref(opts), infos, _stream_ptr(stream))
         out = [{"iters": i.iters, "outer_iters": i.outer_iters, "rel_res": i.rel_res, "converged": i.converged}
                for i in infos]
         if check:

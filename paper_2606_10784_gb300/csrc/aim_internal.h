@@ -282,6 +282,19 @@ aim_status apply_op_multi(MultiLauncher& ml, int count, aim_ctx* const* ctxs, co
                           const double2* const* x, double2* const* y, int precision, cudaStream_t st);
 
 // ------------------------------------------------------------------------------------
+// batched products of concurrent solves (batcher.cu)
+// ------------------------------------------------------------------------------------
+}  // namespace aim
+struct aim_batcher;
+namespace aim {
+// the batcher attached to the calling thread by aim_solve_batched (nullptr outside it)
+aim_batcher* current_batcher();
+// y = A x for one solve, fused with the products that other solves of the batcher submit at about
+// the same time; asynchronous: `st` waits for the result on the device
+aim_status batcher_product(aim_batcher* b, aim_ctx* ctx, aim_op op, int nrhs, const double2* x, double2* y,
+                           int precision, cudaStream_t st);
+
+// ------------------------------------------------------------------------------------
 // GMRES (solver.cu)
 // ------------------------------------------------------------------------------------
 aim_status gmres_solve(aim_ctx* ctx, aim_op system, int nrhs, const double2* b, double2* x,

@@ -318,6 +318,15 @@ aim_status dot_norms(const double2* vecs, int n, int nrhs, double2* out, double2
 
 }  // namespace
 
+// The solver's operator products: through the calling thread's batcher when aim_solve_batched
+// attached one (the product then joins other solves' products in a multi-context launch), else
+// directly.
+static aim_status solver_apply(aim_ctx* ctx, aim_op op, int nrhs, const double2* x, double2* y, int precision,
+                               cudaStream_t st) {
+  if (aim_batcher* b = current_batcher()) return batcher_product(b, ctx, op, nrhs, x, y, precision, st);
+  return apply_op(ctx, op, nrhs, x, y, precision, st);
+}
+
 // The operator product of an Arnoldi step always reads the current vector and writes w, so it is
 // captured once as a CUDA graph and replayed each iteration: one host call instead of ~10 kernel
 // launches, which is what limits small problems. Not while kernels are being timed (a replay
@@ -328,7 +337,7 @@ struct OpGraph {
   long long counts[K_COUNT] = {};   // launches one replay stands for, per kernel id
   void capture(aim_ctx* ctx, aim_op op, int nrhs, const double2* x, double2* y, int precision, cudaStream_t st) {
     tried = true;
-    if (profiling_active()) return;
+    if (profiling_active() || current_batcher() != nullptr) return;   // batched products are not captured
     long long before[K_COUNT], after[K_COUNT];
     thread_launch_counts(before);
     if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -480,7 +489,7 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
 
   while (true) {
     // true residual r = b - A x
-    AIM_TRY(apply_op(ctx, op, nrhs, x, ws.w, precision, st));
+    AIM_TRY(solver_apply(ctx, op, nrhs, x, ws.w, precision, st));
     count_launches(K_GMRES, 1);
     k_residual<<<nb, tpb, 0, st>>>(b, ws.w, (int)vsz, ws.r);
     AIM_CUDA_TRY(cudaGetLastError());
@@ -522,7 +531,7 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
       if (op_graph.exec != nullptr) {
         AIM_TRY(op_graph.replay(st));
       } else {
-        AIM_TRY(apply_op(ctx, op, nrhs, ws.cur, ws.w, precision, st));
+        AIM_TRY(solver_apply(ctx, op, nrhs, ws.cur, ws.w, precision, st));
       }
       // CGS2 (3 launches here + 2 x 2 in multidot_df + 2 x 2 in vcombine_df + 2 in dot_norms),
       // timed as one group when profiling
@@ -645,7 +654,7 @@ aim_status gmres_solve(aim_ctx* ctx, aim_op system, int nrhs, const double2* b, 
     aim_status s = AIM_OK;
     for (int outer_it = 0; outer_it < 60; ++outer_it) {
       // r = b - A x (FP64)
-      s = apply_op(ctx, system, nrhs, x, rr, AIM_FP64, st);
+      s = solver_apply(ctx, system, nrhs, x, rr, AIM_FP64, st);
       if (s != AIM_OK) break;
       count_launches(K_GMRES, 3);
       k_residual<<<blocks_for((long long)vsz, 256), 256, 0, st>>>(b, rr, (int)vsz, rr);

@@ -4,7 +4,9 @@ Requests (a contour, a wavenumber, grid and filter parameters, and 1..16 inciden
 arrive over time. The server admits a request when a slot is free and the device-memory
 bound of its context (aim_query_solve_bytes) fits in the remaining budget, runs it on that slot's
 own CUDA stream, and reports each request's latency from arrival to completion. Slots run
-concurrently, so the device work of requests admitted at different times overlaps.
+concurrently, so the device work of requests admitted at different times overlaps; with fusion on
+(the default) the slots share an aim_batcher, and the operator products of requests running at
+the same time go into one multi-context launch per grid-pass stage (grids of one size class).
 Contexts (kernel spectra, projections, near field, Krylov workspace) stay resident in an LRU
 cache keyed by the request's geometry and parameters, so a repeated geometry skips setup.
 
@@ -77,14 +79,18 @@ class Server:
     """Admission by device-memory budget, `slots` concurrent solves, resident context cache."""
 
     def __init__(self, memory_budget_bytes: int, slots: int = 4, max_cached: int = 16, device: int = 0,
-                 policy: str = "sjf", max_wait_s: float = 30.0):
+                 policy: str = "sjf", max_wait_s: float = 30.0, fused: bool = True, fuse_wait_us: int = 50):
         """policy "fifo": the first queued request that fits. policy "sjf": the fitting request
         with the least estimated work (right-hand sides x grid cells x unknowns, which tracks
         the grid work per iteration times the iteration count), except that requests waiting
-        longer than max_wait_s go first, oldest first, so that large requests are not starved."""
+        longer than max_wait_s go first, oldest first, so that large requests are not starved.
+        fused: the slots' solves share an aim_batcher, so the operator products of requests that
+        run at the same time (grids up to P = 512, one size class) go into one multi-context
+        launch per grid-pass stage; fuse_wait_us bounds how long a product waits for partners."""
         import torch
         if policy not in ("fifo", "sjf"):
             raise ValueError("policy must be 'fifo' or 'sjf'")
+        self.batcher = aim.Batcher(fuse_wait_us) if fused else None
         self.policy = policy
         self.max_wait_s = float(max_wait_s)
         self.torch = torch
@@ -139,6 +145,12 @@ class Server:
         for ctx, _ in self._cache.values():
             ctx.close()
         self._cache.clear()
+        if self.batcher is not None:
+            self.batcher.close()
+            self.batcher = None
+
+    def fusion_stats(self) -> Optional[dict]:
+        return self.batcher.stats() if self.batcher is not None else None
 
     @property
     def refused(self) -> List[int]:
@@ -223,7 +235,8 @@ class Server:
                     x = torch.zeros_like(rhs)
                 ctx.rhs_planewave(req.angles, rhs, stream=stream)
                 status, info = ctx.solve(req.system, rhs, x, tol=req.tol, restart=req.restart,
-                                         max_iter=req.max_iter, precision=req.precision, stream=stream, check=False)
+                                         max_iter=req.max_iter, precision=req.precision, stream=stream, check=False,
+                                         batcher=self.batcher)
                 stream.synchronize()
                 x_host = x.cpu().numpy()
             except aim.AimError as e:

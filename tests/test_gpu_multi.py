@@ -94,3 +94,59 @@ def test_multi_context_rejects_bad_calls(mixed_sizes):
     with pytest.raises(aim.AimError) as exc:
         aim.matvec_multi([ctxs[0]], ["S"], [x.cpu()], [y])
     assert exc.value.status == aim.EINVAL
+
+
+# --------------------------------------------------------------------------------------
+# fused products of concurrent solves (aim_batcher, aim_solve_batched)
+# --------------------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [0, 1])
+def test_concurrent_batched_solves_equal_solo_solves(mixed_sizes, precision):
+    import threading
+    aim, ctxs, nodes = mixed_sizes
+    use = [1, 2, 3]                                   # P = 128, 256, 512: fusible size classes
+    circ = synth.circle_polygon(2.0, 200)
+    extra = aim.Context(circ, K, aim.TE, 96, fft_P=256, alpha=3.0 * K)   # a second P = 256 context
+    pairs = [(ctxs[i], nodes[i]) for i in use] + [(extra, circ)]
+    try:
+        rhs = []
+        for c, nd in pairs:
+            r = torch.empty((2, len(nd)), dtype=torch.complex128, device="cuda")
+            c.rhs_planewave([0.0, 1.0], r)
+            rhs.append(r)
+        torch.cuda.synchronize()
+        kw = dict(tol=1e-8, restart=300, max_iter=2000, precision=precision, inner_tol=0.0)
+        solo = []
+        for (c, nd), r in zip(pairs, rhs):
+            x = torch.zeros_like(r)
+            info = c.solve("calderon_alpha", r, x, **kw)
+            solo.append((x, info))
+        batcher = aim.Batcher(max_wait_us=500)
+        out = [None] * len(pairs)
+        errors = []
+
+        def work(i):
+            try:
+                c, nd = pairs[i]
+                s = torch.cuda.Stream()
+                x = torch.zeros_like(rhs[i])
+                info = c.solve("calderon_alpha", rhs[i], x, stream=s, batcher=batcher, **kw)
+                s.synchronize()
+                out[i] = (x, info)
+            except Exception as e:   # reported below
+                errors.append(repr(e))
+
+        threads = [threading.Thread(target=work, args=(i,)) for i in range(len(pairs))]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join(timeout=300)
+        assert not errors, errors
+        stats = batcher.stats()
+        batcher.close()
+        for (xb, ib), (xs, is_) in zip(out, solo):
+            assert ib == is_
+            assert torch.equal(xb, xs)
+        assert stats["fused_products"] > 0, stats
+        print("batcher:", stats)
+    finally:
+        extra.close()
