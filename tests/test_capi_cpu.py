@@ -117,3 +117,27 @@ def test_binding_refuses_to_run_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(aim, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError):
         aim.lib()
+
+
+def test_new_entry_points_reject_bad_arguments_before_the_gpu(lib):
+    from paper_2606_10784_gb300 import aim
+    i = ctypes.c_int
+    assert lib.aim_batcher_create(-1, ctypes.byref(ctypes.c_void_p())) == aim.EINVAL
+    assert lib.aim_batcher_create(200, None) == aim.EINVAL
+    assert lib.aim_batcher_stats(None, None, None, None) == aim.EINVAL
+    assert lib.aim_solve_batched(None, None, 0, 1, None, None, 0, None, None, None) == aim.EINVAL
+    assert lib.aim_kernel_table(None, 0, None, None) == aim.EINVAL
+    a = (ctypes.c_double * 4)()
+    assert lib.aim_lanczos_bidiag(None, 0, 4, 0, None, a, a, None, None, None) == aim.EINVAL
+    assert lib.aim_matvec_multi(0, None, None, None, None, None, 0, None) == aim.EINVAL
+    assert lib.aim_matvec_multi(33, None, None, None, None, None, 0, None) == aim.EINVAL
+    lib.aim_batcher_destroy(None)        # NULL is allowed
+
+
+def test_setup_rejects_unknown_filter_kind(lib):
+    from paper_2606_10784_gb300 import aim
+    nodes = synth.circle_polygon(1.0, 64)
+    for kind in (-1, 3):
+        with pytest.raises(aim.AimError) as exc:
+            aim.Context(nodes, 2 * np.pi, aim.TE, 32, alpha=4.0 * np.pi, filter_kind=kind)
+        assert exc.value.status == aim.EINVAL

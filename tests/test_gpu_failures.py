@@ -160,3 +160,36 @@ def test_context_used_on_another_device_is_refused(aimlib):
     finally:
         torch.cuda.set_device(0)
         ctx.close()
+
+
+def test_new_entry_points_report_misuse(aimlib):
+    nodes = synth.circle_polygon(1.0, 64)
+    tm = aimlib.Context(nodes, K, aimlib.TM, 32, alpha=4.0 * K)
+    te = aimlib.Context(nodes, K, aimlib.TE, 32)            # no filter radius
+    te2 = aimlib.Context(synth.circle_polygon(1.5, 96), K, aimlib.TE, 40, alpha=3.0 * K)
+    try:
+        v0 = torch.ones(64, dtype=torch.complex128, device="cuda")
+        # Lanczos: TM collocation operators are not symmetric; k beyond n
+        with pytest.raises(aimlib.AimError) as exc:
+            tm.lanczos_bidiag("S", 8, v0)
+        assert exc.value.status == aimlib.ESTATE
+        with pytest.raises(aimlib.AimError) as exc:
+            te.lanczos_bidiag("S", 65, v0)
+        assert exc.value.status == aimlib.EINVAL
+        # the analytic filter needs a filter radius
+        out = torch.empty((33, 33), dtype=torch.complex128, device="cuda")
+        with pytest.raises(aimlib.AimError) as exc:
+            te.kernel_table(aimlib.TABLE_ANALYTIC_SAMPLES, out)
+        assert exc.value.status == aimlib.ESTATE
+        # one multi-context launch needs one pass geometry: change one context's schedule
+        te2.set_schedule(aimlib.FP64, 2, 128, 0, 16)
+        xs = [torch.ones((1, 64), dtype=torch.complex128, device="cuda"),
+              torch.ones((1, 96), dtype=torch.complex128, device="cuda")]
+        ys = [torch.empty_like(x) for x in xs]
+        with pytest.raises(aimlib.AimError) as exc:
+            aimlib.matvec_multi([te, te2], ["S", "S"], xs, ys, precision=aimlib.FP64)
+        assert exc.value.status == aimlib.EINVAL
+        assert "geometry" in str(exc.value)
+    finally:
+        for c in (tm, te, te2):
+            c.close()
