@@ -43,7 +43,10 @@ def make_requests(sv, n=8, seed=3):
     return reqs
 
 
-def test_results_identical_alone_and_mixed(serving):
+@pytest.mark.parametrize("fused", [False, True])
+def test_results_identical_alone_and_mixed(serving, fused):
+    # fused: the slots' solves share a batcher, so products of concurrent requests run in
+    # multi-context launches; every request's arithmetic is unchanged, so the results are too
     aim, sv = serving
     reqs = make_requests(sv)
     alone = {}
@@ -55,11 +58,14 @@ def test_results_identical_alone_and_mixed(serving):
     for res_i in res:
         alone[res_i.rid] = res_i
     assert len(alone) == len(reqs)
-    srv = sv.Server(memory_budget_bytes=8 << 30, slots=4)
+    srv = sv.Server(memory_budget_bytes=8 << 30, slots=4, fused=fused)
     for r in make_requests(sv):
         srv.submit(r)
     mixed = {r.rid: r for r in srv.drain(timeout=600)}
+    stats = srv.fusion_stats()
     srv.close()
+    if fused:
+        assert stats["products"] > 0
     for rid, a in alone.items():
         b = mixed[rid]
         assert a.status == 0 and b.status == 0
