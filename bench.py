@@ -247,12 +247,27 @@ def _kernel_table(prof):
             for k, v in prof.items()}
 
 
+_STREAM = None
+
+
+def solve_stream():
+    """The stream every timed solve runs on. A solve on a stream of its own captures its Arnoldi
+    step's operator product as a CUDA graph and replays it (the legacy default stream cannot be
+    captured), as a user's solve on its own stream would; torch's events record on it too."""
+    global _STREAM
+    if _STREAM is None:
+        import torch
+        _STREAM = torch.cuda.Stream()
+    return _STREAM
+
+
 def _solve_once(aim, wl, prec, rhs, x, last=None):
-    ctx = aim.Context(wl.nodes, wl.k, aim.TE, wl.m, fft_P=wl.fft_P, alpha=wl.alpha)
-    ctx.rhs_planewave(wl.angles, rhs)
+    st = solve_stream()
+    ctx = aim.Context(wl.nodes, wl.k, aim.TE, wl.m, fft_P=wl.fft_P, alpha=wl.alpha, stream=st)
+    ctx.rhs_planewave(wl.angles, rhs, stream=st)
     x.zero_()
     info = ctx.solve("calderon_alpha", rhs, x, tol=SOLVE_TOL, restart=RESTART, max_iter=6000, precision=prec,
-                     inner_tol=0.0)
+                     inner_tol=0.0, stream=st)
     if last is not None:
         last["info"] = info[0]
         last["ctx_info"] = ctx.info()
@@ -264,11 +279,14 @@ def single_solve_line(aim, wl, precision, steps, warmup, world, rank, dev, barri
     step for the per-kernel table and the roofline. Returns the pieces of the JSON line."""
     import torch
     prec = {"fp64": aim.FP64, "mixed": aim.MIXED, "native": aim.FP64_NATIVE}[precision]
-    rhs = torch.empty((1, wl.n), dtype=torch.complex128, device=dev)
-    x = torch.zeros_like(rhs)
+    st = solve_stream()
+    with torch.cuda.stream(st):
+        rhs = torch.empty((1, wl.n), dtype=torch.complex128, device=dev)
+        x = torch.zeros_like(rhs)
     last = {}
-    for _ in range(warmup):
-        _solve_once(aim, wl, prec, rhs, x, last)
+    with torch.cuda.stream(st):
+        for _ in range(warmup):
+            _solve_once(aim, wl, prec, rhs, x, last)
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -277,10 +295,11 @@ def single_solve_line(aim, wl, precision, steps, warmup, world, rank, dev, barri
     l0 = aim.launch_count()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        _solve_once(aim, wl, prec, rhs, x, last)
-    e1.record()
+    with torch.cuda.stream(st):
+        e0.record()
+        for _ in range(steps):
+            _solve_once(aim, wl, prec, rhs, x, last)
+        e1.record()
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
@@ -291,7 +310,8 @@ def single_solve_line(aim, wl, precision, steps, warmup, world, rank, dev, barri
     if with_profile:
         # one more step with every launch bracketed by CUDA events on its own stream
         aim.profile_start()
-        _solve_once(aim, wl, prec, rhs, x)
+        with torch.cuda.stream(st):
+            _solve_once(aim, wl, prec, rhs, x)
         torch.cuda.synchronize()
         prof = aim.profile_stop()
     return elapsed, launches, clocks, prof, last
@@ -332,9 +352,10 @@ def gb300_arm(args):
         c0.rhs_planewave(wl.angles, rhs_h)
 
     def step_e2e():
-        ctx = aim.Context(wl.nodes, wl.k, aim.TE, wl.m, fft_P=wl.fft_P, alpha=wl.alpha)
+        st = solve_stream()
+        ctx = aim.Context(wl.nodes, wl.k, aim.TE, wl.m, fft_P=wl.fft_P, alpha=wl.alpha, stream=st)
         ctx.solve("calderon_alpha", rhs_h, x_h, tol=SOLVE_TOL, restart=RESTART, max_iter=6000, precision=prec,
-                  inner_tol=0.0)
+                  inner_tol=0.0, stream=st)
         ctx.close()
 
     e2e_steps = max(1, min(args.steps, E2E_STEPS_MAX))
@@ -490,29 +511,33 @@ def batching_arm(args, aim=None, steps=None, warmup=None):
     x = torch.zeros_like(rhs)
     last = {}
 
+    sm = solve_stream()
+
     def step(solve=True):
-        ctx = aim.Context(wl.nodes, wl.k, aim.TE, wl.m, fft_P=wl.fft_P, alpha=wl.alpha)
-        last["schedule"] = ctx.autotune(nrhs=R, precision=prec)
-        ctx.rhs_planewave(wl.angles, rhs)
+        ctx = aim.Context(wl.nodes, wl.k, aim.TE, wl.m, fft_P=wl.fft_P, alpha=wl.alpha, stream=sm)
+        last["schedule"] = ctx.autotune(nrhs=R, precision=prec, stream=sm)
+        ctx.rhs_planewave(wl.angles, rhs, stream=sm)
         x.zero_()
         if solve:
             st, info = ctx.solve("calderon_alpha", rhs, x, tol=SOLVE_TOL, restart=RESTART, max_iter=6000,
-                                 precision=prec, inner_tol=0.0, check=False)
+                                 precision=prec, inner_tol=0.0, check=False, stream=sm)
             last["status"], last["info"] = st, info
         else:   # warm-up: setup, autotune and one batched product load every kernel
-            ctx.matvec("calderon_alpha", rhs, x, precision=prec)
+            ctx.matvec("calderon_alpha", rhs, x, precision=prec, stream=sm)
         ctx.close()
 
-    for _ in range(warmup):
-        step(solve=False)
+    with torch.cuda.stream(sm):
+        for _ in range(warmup):
+            step(solve=False)
     torch.cuda.synchronize()
     l0 = aim.launch_count()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        step()
-    e1.record()
+    with torch.cuda.stream(sm):
+        e0.record()
+        for _ in range(steps):
+            step()
+        e1.record()
     torch.cuda.synchronize()
     el = e0.elapsed_time(e1) / 1e3
     its = [i["iters"] for i in last["info"]]
