@@ -187,6 +187,41 @@ aim_status aim_setup(const aim_geometry* geometry, double k, const aim_grid* gri
 /* Releases everything the context owns. NULL is allowed. */
 void aim_destroy(aim_ctx* ctx);
 
+/* Setup artefacts, saved and reloaded (no counterpart in the paper: a restarted process reloads
+ * them instead of recomputing them). A setup blob holds what aim_setup computes: the active grid
+ * set and the projections P = Lambda W Phi (Sec. III-A, Eq. 7), the twiddles, G^-1 (Eq. 3), the
+ * near-field correction, and the kernel spectrum and filtered spectrum (Sec. III-B, Eq. 10) in
+ * FP64. Their complex64 and double-float copies are derived again on import, exactly as aim_setup
+ * derives them, so a context made by aim_import_setup gives bit-identical results.
+ *
+ * aim_setup_key: a 64-bit key (FNV-1a) of everything aim_setup's result depends on: the form,
+ * the vertices, k, the derived grid (m, P, L, eps), s, quad_p, the near radius and the filter.
+ * Two calls whose arguments describe the same problem (e.g. fft_P = 0 and the P it selects) get
+ * the same key. Host only: no CUDA call. Errors: those of aim_setup's argument checks.
+ *
+ * aim_export_setup: with buf == NULL, sets *bytes to the blob's size. Otherwise *bytes is the
+ * size of the host buffer `buf` (AIM_EINVAL if smaller than the blob) and receives the size
+ * written. The blob is a 160-byte header (magic "AIMSETUP", format version, key, problem
+ * parameters, array counts, a checksum of the payload) followed by the arrays, each starting
+ * at a 16-byte offset, little-endian. Copies run on `stream`; the call synchronises it. The
+ * caller owns `buf`.
+ *
+ * aim_import_setup: a context equal to aim_setup(geometry, k, grid, stencil, filter, ...) from a
+ * blob that aim_export_setup wrote for that problem. Before any CUDA call it checks the magic,
+ * the version, the size, the checksum, every problem parameter and vertex against the
+ * arguments, and every index of the stored sparse patterns against its range: AIM_EINVAL
+ * (with the reason in aim_last_error) if any differs, so a blob of another problem, a stale
+ * format or a corrupted file is refused and never reaches the device. `blob` is host memory,
+ * read only during the call. Then as aim_setup: AIM_ENOMEM, AIM_ECUDA; on success *out owns
+ * its device state until aim_destroy. */
+aim_status aim_setup_key(const aim_geometry* geometry, double k, const aim_grid* grid,
+                         const aim_stencil* stencil, const aim_filter* filter,
+                         unsigned long long* key);
+aim_status aim_export_setup(const aim_ctx* ctx, void* buf, size_t* bytes, void* stream);
+aim_status aim_import_setup(const aim_geometry* geometry, double k, const aim_grid* grid,
+                            const aim_stencil* stencil, const aim_filter* filter, const void* blob,
+                            size_t bytes, void* stream, aim_ctx** out);
+
 aim_status aim_get_info(const aim_ctx* ctx, aim_info* info);
 
 /* Pre-allocates workspaces for up to nrhs simultaneous vectors in the given precision,

@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import threading
 from typing import Optional
 
 import numpy as np
@@ -112,6 +113,14 @@ def lib() -> ctypes.CDLL:
                             ctypes.POINTER(Filter), vp, ctypes.POINTER(vp)]
     L.aim_setup.restype = i
     L.aim_destroy.argtypes = [vp]
+    L.aim_setup_key.argtypes = [ctypes.POINTER(Geometry), d, ctypes.POINTER(Grid), ctypes.POINTER(Stencil),
+                                ctypes.POINTER(Filter), ctypes.POINTER(ctypes.c_ulonglong)]
+    L.aim_setup_key.restype = i
+    L.aim_export_setup.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t), vp]
+    L.aim_export_setup.restype = i
+    L.aim_import_setup.argtypes = [ctypes.POINTER(Geometry), d, ctypes.POINTER(Grid), ctypes.POINTER(Stencil),
+                                   ctypes.POINTER(Filter), vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+    L.aim_import_setup.restype = i
     L.aim_destroy.restype = None
     L.aim_get_info.argtypes = [vp, ctypes.POINTER(Info)]
     L.aim_get_info.restype = i
@@ -272,23 +281,104 @@ def query_solve_bytes(nodes, form: int, m: int, s: int = 4, quad_p: int = 4, fft
     return out.value
 
 
+def _setup_args(nodes, form, m, fft_P, L, s, quad_p, near_radius, alpha, filter_kind):
+    g, keep = _geometry(nodes, form, quad_p)
+    flt = Filter(int(filter_kind) if alpha is not None else FILTER_NONE, float(alpha) if alpha is not None else 0.0)
+    return g, keep, Grid(int(m), float(L), int(fft_P)), Stencil(int(s), float(near_radius)), flt
+
+
+def setup_key(nodes, k: float, form: int, m: int, fft_P: int = 0, L: float = 0.0, s: int = 4, quad_p: int = 4,
+              near_radius: float = 0.0, alpha: Optional[float] = None, filter_kind: int = FILTER_NUMERICAL) -> str:
+    """aim_setup_key of a problem (Context's arguments) as 16 hex digits; host only."""
+    g, keep, grid, sten, flt = _setup_args(nodes, form, m, fft_P, L, s, quad_p, near_radius, alpha, filter_kind)
+    key = ctypes.c_ulonglong(0)
+    _check(lib().aim_setup_key(ctypes.byref(g), float(k), ctypes.byref(grid), ctypes.byref(sten), ctypes.byref(flt),
+                               ctypes.byref(key)), "aim_setup_key")
+    return "%016x" % key.value
+
+
+class SetupCache:
+    """Setup blobs on disk, one file per problem key, so that a restarted process reloads its
+    contexts (aim_import_setup) instead of recomputing them. A file that the library refuses
+    (another format version, a corrupted or truncated write, a key collision) is rebuilt and
+    replaced; files are written to a temporary name and renamed, so readers never see half a blob."""
+
+    SUFFIX = ".aimsetup"
+
+    def __init__(self, directory: str):
+        self.directory = os.path.abspath(directory)
+        os.makedirs(self.directory, exist_ok=True)
+        self.hits = 0
+        self.misses = 0
+        self.rejected = 0
+        self._lock = threading.Lock()
+
+    def path(self, key: str) -> str:
+        return os.path.join(self.directory, key + self.SUFFIX)
+
+    def context(self, nodes, k: float, form: int, m: int, stream=None, **kw) -> "Context":
+        """The problem's context: imported from its blob when the directory holds a valid one,
+        else set up and its blob written."""
+        key = setup_key(nodes, k, form, m, **kw)
+        path = self.path(key)
+        if os.path.exists(path):
+            blob = np.fromfile(path, dtype=np.uint8)
+            try:
+                ctx = Context(nodes, k, form, m, stream=stream, blob=blob, **kw)
+                with self._lock:
+                    self.hits += 1
+                return ctx
+            except AimError as e:
+                if e.status != EINVAL:
+                    raise
+                with self._lock:
+                    self.rejected += 1
+        ctx = Context(nodes, k, form, m, stream=stream, **kw)
+        with self._lock:
+            self.misses += 1
+        tmp = "%s.%d.%d.tmp" % (path, os.getpid(), threading.get_ident())
+        ctx.export_setup(stream).tofile(tmp)
+        os.replace(tmp, path)
+        return ctx
+
+    def stats(self) -> dict:
+        with self._lock:
+            return {"hits": self.hits, "misses": self.misses, "rejected": self.rejected}
+
+
 class Context:
     """One AIM operator set on the current CUDA device (wraps aim_ctx*)."""
 
     def __init__(self, nodes, k: float, form: int, m: int, fft_P: int = 0, L: float = 0.0, s: int = 4,
                  quad_p: int = 4, near_radius: float = 0.0, alpha: Optional[float] = None, stream=None,
-                 filter_kind: int = FILTER_NUMERICAL):
-        g, keep = _geometry(nodes, form, quad_p)
-        flt = Filter(int(filter_kind) if alpha is not None else FILTER_NONE, float(alpha) if alpha is not None else 0.0)
+                 filter_kind: int = FILTER_NUMERICAL, blob=None):
+        """aim_setup of the problem; with `blob` (bytes or a uint8 array from export_setup),
+        aim_import_setup of it instead, which refuses a blob of any other problem (EINVAL)."""
+        g, keep, grid, sten, flt = _setup_args(nodes, form, m, fft_P, L, s, quad_p, near_radius, alpha, filter_kind)
         h = ctypes.c_void_p()
-        _check(lib().aim_setup(ctypes.byref(g), float(k), ctypes.byref(Grid(int(m), float(L), int(fft_P))),
-                               ctypes.byref(Stencil(int(s), float(near_radius))), ctypes.byref(flt),
-                               _stream_ptr(stream), ctypes.byref(h)), "aim_setup")
+        if blob is None:
+            _check(lib().aim_setup(ctypes.byref(g), float(k), ctypes.byref(grid), ctypes.byref(sten),
+                                   ctypes.byref(flt), _stream_ptr(stream), ctypes.byref(h)), "aim_setup")
+        else:
+            buf = np.ascontiguousarray(np.frombuffer(blob, dtype=np.uint8) if isinstance(blob, (bytes, bytearray))
+                                       else np.asarray(blob, dtype=np.uint8).reshape(-1))
+            _check(lib().aim_import_setup(ctypes.byref(g), float(k), ctypes.byref(grid), ctypes.byref(sten),
+                                          ctypes.byref(flt), buf.ctypes.data, buf.size, _stream_ptr(stream),
+                                          ctypes.byref(h)), "aim_import_setup")
         self._h = h
         self.form = form
         inf = self.info()
         self.n = inf["n"]
         self.m = inf["m"]
+
+    def export_setup(self, stream=None) -> np.ndarray:
+        """The context's setup blob (aim_export_setup) as a uint8 array."""
+        size = ctypes.c_size_t(0)
+        _check(lib().aim_export_setup(self._h, None, ctypes.byref(size), _stream_ptr(stream)), "aim_export_setup")
+        buf = np.empty(size.value, dtype=np.uint8)
+        _check(lib().aim_export_setup(self._h, buf.ctypes.data, ctypes.byref(size), _stream_ptr(stream)),
+               "aim_export_setup")
+        return buf
 
     def close(self):
         if getattr(self, "_h", None):

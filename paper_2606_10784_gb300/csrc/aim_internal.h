@@ -157,6 +157,8 @@ struct aim_ctx {
   // Gram inverse, row i: entries for columns (i + d) mod n, d = -band..band
   double* gram_inv = nullptr;
   int gram_band = 0;
+  // entry counts of the scatter and gather lists and of gram_inv (for aim_export_setup)
+  size_t n_sc = 0, n_ga = 0, n_gram = 0;
   // geometry: host copy and device vertices
   std::vector<double> xy;
   double2* nodes = nullptr;
@@ -225,6 +227,13 @@ struct HostSetup {
 };
 
 aim_status host_setup(aim_ctx* ctx, HostSetup* hs);
+// argument checks of aim_setup, and the context's sizes and grid parameters from them (host only)
+aim_status validate_setup(const aim_geometry* g, double k, const aim_grid* grid, const aim_stencil* st,
+                          const aim_filter* f);
+aim_status derive_params(aim_ctx* ctx, const aim_geometry* geometry, double k, const aim_grid* grid,
+                         const aim_stencil* stencil, const aim_filter* filter);
+// FP64, complex64 and double-float twiddle tables of ctx->P from 2P doubles (re, im)
+aim_status upload_twiddles(aim_ctx* ctx, const double* tw2, cudaStream_t st);
 double host_grid_half_side(const double* xy, int n, int m, int s);
 void gauss_legendre01(int n, std::vector<double>* x, std::vector<double>* w);
 
@@ -235,6 +244,9 @@ void gauss_legendre01(int n, std::vector<double>* x, std::vector<double>* w);
 aim_status device_spectra_and_near(aim_ctx* ctx, const HostSetup& hs, cudaStream_t st);
 // the grid kernel tables of aim_kernel_table (natural order, (H+1)^2 complex128, device `out`)
 aim_status kernel_table(aim_ctx* ctx, int which, double2* out, cudaStream_t st);
+// f[i] = complex64 rounding of src[i]; df[i] = its double-float split (hi, lo per part), when
+// df is not null: the derived copies aim_setup makes of each FP64 spectrum and near-field value
+aim_status derive_narrow_copies(const double2* src, size_t count, float2* f, float4* df, cudaStream_t st);
 aim_status device_rhs_planewave(aim_ctx* ctx, int nrhs, const double* angles_dev, double2* out, cudaStream_t st);
 
 // ------------------------------------------------------------------------------------

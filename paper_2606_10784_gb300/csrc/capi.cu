@@ -302,6 +302,75 @@ aim_status apply_op_multi(MultiLauncher& ml, int count, aim_ctx* const* ctxs, co
   return AIM_OK;
 }
 
+// e^{-2 pi i t / P}, t < P, from its FP64 (re, im) pairs: the FP64, complex64 and double-float
+// (hi, lo) copies the three grid precisions read.
+aim_status upload_twiddles(aim_ctx* ctx, const double* tw2, cudaStream_t st) {
+  const int P = ctx->P;
+  std::vector<double2> tw(P);
+  std::vector<float2> twf(P);
+  std::vector<float4> twdf(P);
+  for (int t = 0; t < P; ++t) {
+    const double c = tw2[2 * t], s = tw2[2 * t + 1];
+    const float ch = (float)c, sh = (float)s;
+    tw[t] = double2{c, s};
+    twf[t] = float2{ch, sh};
+    twdf[t] = float4{ch, (float)(c - (double)ch), sh, (float)(s - (double)sh)};
+  }
+  AIM_TRY(upload(ctx, &ctx->tw, tw, st));
+  AIM_TRY(upload(ctx, &ctx->twf, twf, st));
+  AIM_TRY(upload(ctx, &ctx->twdf, twdf, st));
+  return AIM_OK;
+}
+
+aim_status validate_setup(const aim_geometry* g, double k, const aim_grid* grid, const aim_stencil* st,
+                           const aim_filter* f) {
+  if (!g || !grid || !st || !g->xy) return fail(AIM_EINVAL, "null argument");
+  if (g->n_seg < 3) return fail(AIM_EINVAL, "n_seg must be >= 3");
+  if (g->form != AIM_TM_PULSE_COLLOC && g->form != AIM_TE_P1_GALERKIN) return fail(AIM_EINVAL, "unknown form");
+  if (g->quad_p < 1 || g->quad_p > 16) return fail(AIM_EINVAL, "quad_p must be in 1..16");
+  if (!(k > 0.0) || !std::isfinite(k)) return fail(AIM_EINVAL, "k must be positive and finite");
+  if (grid->m < 8) return fail(AIM_EINVAL, "m must be >= 8");
+  if (st->s < 2 || st->s > 12) return fail(AIM_EINVAL, "stencil s must be in 2..12");
+  if (grid->fft_P != 0 && (!is_pow2(grid->fft_P) || grid->fft_P < 2 * grid->m - 1))
+    return fail(AIM_EINVAL, "fft_P must be a power of two >= 2m-1");
+  if (f && (f->enabled < AIM_FILTER_NONE || f->enabled > AIM_FILTER_ANALYTIC))
+    return fail(AIM_EINVAL, "filter kind must be AIM_FILTER_NONE, AIM_FILTER_NUMERICAL or AIM_FILTER_ANALYTIC");
+  if (f && f->enabled && !(f->alpha > k) && std::isfinite(f->alpha)) return fail(AIM_EINVAL, "filter radius alpha must exceed k");
+  if (f && f->enabled && !std::isfinite(f->alpha)) return fail(AIM_EINVAL, "filter radius alpha must be finite");
+  for (int i = 0; i < 2 * g->n_seg; ++i)
+    if (!std::isfinite(g->xy[i])) return fail(AIM_EINVAL, "non-finite vertex coordinate");
+  return AIM_OK;
+}
+
+// The sizes and grid parameters of a context from the caller's description (no device work).
+aim_status derive_params(aim_ctx* ctx, const aim_geometry* geometry, double k, const aim_grid* grid,
+                                const aim_stencil* stencil, const aim_filter* filter) {
+  ctx->form = geometry->form;
+  ctx->n = geometry->n_seg;
+  ctx->m = grid->m;
+  ctx->s = stencil->s;
+  ctx->p = geometry->quad_p;
+  ctx->k = k;
+  ctx->xy.assign(geometry->xy, geometry->xy + 2 * (size_t)geometry->n_seg);
+  int P = grid->fft_P;
+  if (P == 0) {
+    P = kMinP;
+    while (P < 2 * grid->m - 1) P *= 2;
+  }
+  if (P > kMaxP) return fail(AIM_EINVAL, "embedding side P exceeds 4096 (m too large)");
+  if (P < kMinP) return fail(AIM_EINVAL, "embedding side P must be >= 64");
+  ctx->P = P;
+  ctx->logP = ilog2(P);
+  ctx->H = P / 2;
+  ctx->logH = ctx->logP - 1;
+  ctx->L = grid->half_side_L > 0.0 ? grid->half_side_L : host_grid_half_side(geometry->xy, ctx->n, ctx->m, ctx->s);
+  ctx->eps = 2.0 * ctx->L / (ctx->m - 1);
+  ctx->near_radius = stencil->near_radius > 0.0 ? stencil->near_radius : ctx->s * ctx->eps;
+  ctx->filter_enabled = filter ? filter->enabled : AIM_FILTER_NONE;
+  ctx->alpha = ctx->filter_enabled ? filter->alpha : 0.0;
+  return AIM_OK;
+}
+
 }  // namespace aim
 
 using namespace aim;
@@ -338,60 +407,11 @@ void aim_destroy(aim_ctx* ctx) {
   delete ctx;
 }
 
-static aim_status validate(const aim_geometry* g, double k, const aim_grid* grid, const aim_stencil* st,
-                           const aim_filter* f) {
-  if (!g || !grid || !st || !g->xy) return fail(AIM_EINVAL, "null argument");
-  if (g->n_seg < 3) return fail(AIM_EINVAL, "n_seg must be >= 3");
-  if (g->form != AIM_TM_PULSE_COLLOC && g->form != AIM_TE_P1_GALERKIN) return fail(AIM_EINVAL, "unknown form");
-  if (g->quad_p < 1 || g->quad_p > 16) return fail(AIM_EINVAL, "quad_p must be in 1..16");
-  if (!(k > 0.0) || !std::isfinite(k)) return fail(AIM_EINVAL, "k must be positive and finite");
-  if (grid->m < 8) return fail(AIM_EINVAL, "m must be >= 8");
-  if (st->s < 2 || st->s > 12) return fail(AIM_EINVAL, "stencil s must be in 2..12");
-  if (grid->fft_P != 0 && (!is_pow2(grid->fft_P) || grid->fft_P < 2 * grid->m - 1))
-    return fail(AIM_EINVAL, "fft_P must be a power of two >= 2m-1");
-  if (f && (f->enabled < AIM_FILTER_NONE || f->enabled > AIM_FILTER_ANALYTIC))
-    return fail(AIM_EINVAL, "filter kind must be AIM_FILTER_NONE, AIM_FILTER_NUMERICAL or AIM_FILTER_ANALYTIC");
-  if (f && f->enabled && !(f->alpha > k) && std::isfinite(f->alpha)) return fail(AIM_EINVAL, "filter radius alpha must exceed k");
-  if (f && f->enabled && !std::isfinite(f->alpha)) return fail(AIM_EINVAL, "filter radius alpha must be finite");
-  for (int i = 0; i < 2 * g->n_seg; ++i)
-    if (!std::isfinite(g->xy[i])) return fail(AIM_EINVAL, "non-finite vertex coordinate");
-  return AIM_OK;
-}
-
-// The sizes and grid parameters of a context from the caller's description (no device work).
-static aim_status derive_params(aim_ctx* ctx, const aim_geometry* geometry, double k, const aim_grid* grid,
-                                const aim_stencil* stencil, const aim_filter* filter) {
-  ctx->form = geometry->form;
-  ctx->n = geometry->n_seg;
-  ctx->m = grid->m;
-  ctx->s = stencil->s;
-  ctx->p = geometry->quad_p;
-  ctx->k = k;
-  ctx->xy.assign(geometry->xy, geometry->xy + 2 * (size_t)geometry->n_seg);
-  int P = grid->fft_P;
-  if (P == 0) {
-    P = kMinP;
-    while (P < 2 * grid->m - 1) P *= 2;
-  }
-  if (P > kMaxP) return fail(AIM_EINVAL, "embedding side P exceeds 4096 (m too large)");
-  if (P < kMinP) return fail(AIM_EINVAL, "embedding side P must be >= 64");
-  ctx->P = P;
-  ctx->logP = ilog2(P);
-  ctx->H = P / 2;
-  ctx->logH = ctx->logP - 1;
-  ctx->L = grid->half_side_L > 0.0 ? grid->half_side_L : host_grid_half_side(geometry->xy, ctx->n, ctx->m, ctx->s);
-  ctx->eps = 2.0 * ctx->L / (ctx->m - 1);
-  ctx->near_radius = stencil->near_radius > 0.0 ? stencil->near_radius : ctx->s * ctx->eps;
-  ctx->filter_enabled = filter ? filter->enabled : AIM_FILTER_NONE;
-  ctx->alpha = ctx->filter_enabled ? filter->alpha : 0.0;
-  return AIM_OK;
-}
-
 aim_status aim_setup(const aim_geometry* geometry, double k, const aim_grid* grid, const aim_stencil* stencil,
                      const aim_filter* filter, void* stream, aim_ctx** out) {
   if (!out) return fail(AIM_EINVAL, "out is null");
   *out = nullptr;
-  AIM_TRY(validate(geometry, k, grid, stencil, filter));
+  AIM_TRY(validate_setup(geometry, k, grid, stencil, filter));
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   aim_ctx* ctx = new (std::nothrow) aim_ctx();
@@ -426,26 +446,14 @@ aim_status aim_setup(const aim_geometry* geometry, double k, const aim_grid* gri
     AIM_TRY(upload(ctx, &ctx->prj.sc_w[q], hs.sc_w[q], st));
     AIM_TRY(upload(ctx, &ctx->prj.ga_w[q], hs.ga_w[q], st));
   }
-  const int P = ctx->P;
-  std::vector<double2> tw(P);
-  std::vector<float2> twf(P);
-  for (int t = 0; t < P; ++t) {
-    tw[t] = double2{hs.tw[2 * t], hs.tw[2 * t + 1]};
-    twf[t] = float2{(float)hs.tw[2 * t], (float)hs.tw[2 * t + 1]};
-  }
-  std::vector<float4> twdf(P);
-  for (int t = 0; t < P; ++t) {
-    const double c = hs.tw[2 * t], s = hs.tw[2 * t + 1];
-    const float ch = (float)c, sh = (float)s;
-    twdf[t] = float4{ch, (float)(c - (double)ch), sh, (float)(s - (double)sh)};
-  }
-  AIM_TRY(upload(ctx, &ctx->tw, tw, st));
-  AIM_TRY(upload(ctx, &ctx->twf, twf, st));
-  AIM_TRY(upload(ctx, &ctx->twdf, twdf, st));
+  AIM_TRY(upload_twiddles(ctx, hs.tw.data(), st));
   if (!hs.gram_inv.empty()) {
     AIM_TRY(upload(ctx, &ctx->gram_inv, hs.gram_inv, st));
     ctx->gram_band = hs.gram_band;
   }
+  ctx->n_sc = hs.sc_col.size();
+  ctx->n_ga = hs.ga_act.size();
+  ctx->n_gram = hs.gram_inv.size();
   AIM_TRY(device_spectra_and_near(ctx, hs, st));
   AIM_CUDA_TRY(cudaStreamSynchronize(st));
   ctx->setup_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -733,7 +741,7 @@ static aim_status query_context_bytes(const aim_geometry* geometry, const aim_gr
   if (!geometry || !grid || !stencil || !bytes || nrhs < 1) return fail(AIM_EINVAL, "bad argument");
   if (precision < AIM_FP64 || precision > AIM_FP64_NATIVE) return fail(AIM_EINVAL, "precision must be 0, 1 or 2");
   // k and the filter do not change any size: validate with placeholders
-  AIM_TRY(validate(geometry, 1.0, grid, stencil, nullptr));
+  AIM_TRY(validate_setup(geometry, 1.0, grid, stencil, nullptr));
   aim_ctx tmp;
   AIM_TRY(derive_params(&tmp, geometry, 1.0, grid, stencil, nullptr));
   HostSetup hs;

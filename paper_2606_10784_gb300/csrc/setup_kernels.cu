@@ -149,6 +149,27 @@ __device__ __forceinline__ float4 split_df(double2 v) {
   return float4{xh, __double2float_rn(v.x - (double)xh), yh, __double2float_rn(v.y - (double)yh)};
 }
 
+// The complex64 and double-float copies of FP64 values, rounded as k_pack_spectrum and the
+// near-field kernels round them (a context imported from a setup blob derives them here).
+__global__ void k_narrow_copies(const double2* src, long long count, float2* f, float4* df) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= count) return;
+  const double2 v = src[t];
+  f[t] = float2{(float)v.x, (float)v.y};
+  if (df != nullptr) df[t] = split_df(v);
+}
+
+aim_status derive_narrow_copies(const double2* src, size_t count, float2* f, float4* df, cudaStream_t st) {
+  if (count == 0) return AIM_OK;
+  const int tpb = 256;
+  {
+    ProfScope ps(K_SETUP_PACK, st);
+    k_narrow_copies<<<(unsigned)((count + tpb - 1) / tpb), tpb, 0, st>>>(src, (long long)count, f, df);
+  }
+  AIM_CUDA_TRY(cudaGetLastError());
+  return AIM_OK;
+}
+
 // live[q'] = 0 when the mask zeroes column q' entirely. kappa(p, q') >= kappa(0, q') holds in
 // floating point as well (sqrt is exact on the perfect square q'^2 and monotone, and both are
 // scaled by the same factor), so the column has a kept entry exactly when its p = 0 entry is kept.

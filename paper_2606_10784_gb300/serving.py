@@ -79,7 +79,8 @@ class Server:
     """Admission by device-memory budget, `slots` concurrent solves, resident context cache."""
 
     def __init__(self, memory_budget_bytes: int, slots: int = 4, max_cached: int = 16, device: int = 0,
-                 policy: str = "sjf", max_wait_s: float = 30.0, fused: bool = False, fuse_wait_us: int = 50):
+                 policy: str = "sjf", max_wait_s: float = 30.0, fused: bool = False, fuse_wait_us: int = 50,
+                 setup_cache_dir: Optional[str] = None):
         """policy "fifo": the first queued request that fits. policy "sjf": the fitting request
         with the least estimated work (right-hand sides x grid cells x unknowns, which tracks
         the grid work per iteration times the iteration count), except that requests waiting
@@ -89,11 +90,15 @@ class Server:
         launch per grid-pass stage; fuse_wait_us bounds how long a product waits for partners.
         Off by default: the slots' own streams already overlap the kernels of small requests, and
         on the served stream fusion tied small requests to their partners' pace (p50 1.37 s fused
-        against 1.17 s unfused at the same throughput)."""
+        against 1.17 s unfused at the same throughput).
+        setup_cache_dir: contexts missing from the resident cache are imported from setup blobs in
+        this directory (aim.SetupCache) when present and written there when built, so a restarted
+        server skips their setup."""
         import torch
         if policy not in ("fifo", "sjf"):
             raise ValueError("policy must be 'fifo' or 'sjf'")
         self.batcher = aim.Batcher(fuse_wait_us) if fused else None
+        self.setup_cache = aim.SetupCache(setup_cache_dir) if setup_cache_dir else None
         self.policy = policy
         self.max_wait_s = float(max_wait_s)
         self.torch = torch
@@ -151,6 +156,10 @@ class Server:
         if self.batcher is not None:
             self.batcher.close()
             self.batcher = None
+
+    def setup_stats(self) -> Optional[dict]:
+        """Setup-blob cache hits, misses and refused files, or None without a cache directory."""
+        return self.setup_cache.stats() if self.setup_cache is not None else None
 
     def fusion_stats(self) -> Optional[dict]:
         return self.batcher.stats() if self.batcher is not None else None
@@ -228,7 +237,10 @@ class Server:
             info: list = []
             x_host = np.zeros((len(req.angles), len(req.nodes)), dtype=np.complex128)
             try:
-                if ctx_entry is None:
+                if ctx_entry is None and self.setup_cache is not None:
+                    ctx = self.setup_cache.context(req.nodes, req.k, aim.TE, req.m, fft_P=req.fft_P, s=req.s,
+                                                   quad_p=req.quad_p, alpha=req.alpha, stream=stream)
+                elif ctx_entry is None:
                     ctx = aim.Context(req.nodes, req.k, aim.TE, req.m, fft_P=req.fft_P, s=req.s,
                                       quad_p=req.quad_p, alpha=req.alpha, stream=stream)
                 else:
