@@ -92,50 +92,62 @@ __device__ __forceinline__ void dft_reg(T2 (&v)[R]) {
 template <typename T2> struct TwiddleFromTable { static constexpr bool value = false; };
 template <> struct TwiddleFromTable<double2> { static constexpr bool value = true; };
 
-// twiddles W_{Ns R}^{k r}, r = 1..R-1, then the length-R DFT.
-template <int LOGR, bool INV, typename T2>
-__device__ __forceinline__ void bfly(T2 (&v)[1 << LOGR], int k, int logNs, const T2* __restrict__ tw, int logP) {
+// The twiddles W_{Ns R}^{k r}, r = 1..R-1, of butterfly position k (k != 0): app(r, w) for each.
+// All transforms a thread works on at the same butterfly position share them, so callers apply
+// each factor to all of them before the next one is formed.
+template <int LOGR, typename T2, typename App>
+__device__ __forceinline__ void twiddles(int k, int logNs, const T2* __restrict__ tw, int logP, App app) {
   constexpr int R = 1 << LOGR;
-  if (k != 0) {
-    const int sh = logP - logNs - LOGR;
-    auto app = [&](int r, const T2& w) { v[r] = INV ? cmulc(v[r], w) : cmul(v[r], w); };
-    if constexpr (TwiddleFromTable<T2>::value) {
-      // (r k) << sh < R Ns 2^sh = P: inside the table
+  const int sh = logP - logNs - LOGR;
+  if constexpr (TwiddleFromTable<T2>::value) {
+    // (r k) << sh < R Ns 2^sh = P: inside the table
 #pragma unroll
-      for (int r = 1; r < R; ++r) app(r, ldro(&tw[(r * k) << sh]));
-    } else {
-      const T2 w1 = ldro(&tw[k << sh]);
-      app(1, w1);
-      if constexpr (R > 2) {
-        const T2 w2 = ldro(&tw[(2 * k) << sh]);
-        app(2, w2);
-        const T2 w3 = cmul(w2, w1);
-        app(3, w3);
-        if constexpr (R > 4) {
-          const T2 w4 = ldro(&tw[(4 * k) << sh]);
-          app(4, w4);
-          const T2 w5 = cmul(w4, w1);
-          app(5, w5);
-          const T2 w6 = cmul(w4, w2);
-          app(6, w6);
-          const T2 w7 = cmul(w4, w3);
-          app(7, w7);
-          if constexpr (R > 8) {
-            const T2 w8 = ldro(&tw[(8 * k) << sh]);
-            app(8, w8);
-            app(9, cmul(w8, w1));
-            app(10, cmul(w8, w2));
-            app(11, cmul(w8, w3));
-            app(12, cmul(w8, w4));
-            app(13, cmul(w8, w5));
-            app(14, cmul(w8, w6));
-            app(15, cmul(w8, w7));
-          }
+    for (int r = 1; r < R; ++r) app(r, ldro(&tw[(r * k) << sh]));
+  } else {
+    const T2 w1 = ldro(&tw[k << sh]);
+    app(1, w1);
+    if constexpr (R > 2) {
+      const T2 w2 = ldro(&tw[(2 * k) << sh]);
+      app(2, w2);
+      const T2 w3 = cmul(w2, w1);
+      app(3, w3);
+      if constexpr (R > 4) {
+        const T2 w4 = ldro(&tw[(4 * k) << sh]);
+        app(4, w4);
+        const T2 w5 = cmul(w4, w1);
+        app(5, w5);
+        const T2 w6 = cmul(w4, w2);
+        app(6, w6);
+        const T2 w7 = cmul(w4, w3);
+        app(7, w7);
+        if constexpr (R > 8) {
+          const T2 w8 = ldro(&tw[(8 * k) << sh]);
+          app(8, w8);
+          app(9, cmul(w8, w1));
+          app(10, cmul(w8, w2));
+          app(11, cmul(w8, w3));
+          app(12, cmul(w8, w4));
+          app(13, cmul(w8, w5));
+          app(14, cmul(w8, w6));
+          app(15, cmul(w8, w7));
         }
       }
     }
   }
-  dft_reg<R, INV>(v);
+}
+
+// Twiddles of position k applied to the NF transforms v[f][t][.] (one set of factors for all),
+// then their length-R DFTs.
+template <int LOGR, bool INV, int NF, int NB, typename T2>
+__device__ __forceinline__ void bfly_shared(T2 (&v)[NF][NB][1 << LOGR], int t, int k, int logNs,
+                                            const T2* __restrict__ tw, int logP) {
+  if (k != 0)
+    twiddles<LOGR>(k, logNs, tw, logP, [&](int r, const T2& w) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) v[f][t][r] = INV ? cmulc(v[f][t][r], w) : cmul(v[f][t][r], w);
+    });
+#pragma unroll
+  for (int f = 0; f < NF; ++f) dft_reg<1 << LOGR, INV>(v[f][t]);
 }
 
 template <int LOGE>
@@ -155,14 +167,14 @@ __device__ __forceinline__ void smem_pass(T2* __restrict__ sm, const int (&fb)[N
   const int nsm = (1 << logNs) - 1;
   T2 v[NF][NB][R];
 #pragma unroll
-  for (int f = 0; f < NF; ++f)
+  for (int t = 0; t < NB; ++t) {
+    const int b = j + t * tpf;
 #pragma unroll
-    for (int t = 0; t < NB; ++t) {
-      const int b = j + t * tpf;
+    for (int f = 0; f < NF; ++f)
 #pragma unroll
       for (int r = 0; r < R; ++r) v[f][t][r] = sm[fb[f] + padi<LOGE>(b + (r << lognb))];
-      bfly<LOGR, INV>(v[f][t], b & nsm, logNs, tw, logP);
-    }
+    bfly_shared<LOGR, INV>(v, t, b & nsm, logNs, tw, logP);
+  }
   __syncthreads();
 #pragma unroll
   for (int f = 0; f < NF; ++f)
@@ -192,19 +204,18 @@ __device__ __forceinline__ void last_pass(const T2* __restrict__ sm, const int (
   for (int t = 0; t < NB; ++t) {
     const int b = j + t * tpf;
     const int k = b & nsm;
-    T2 v[NF][R];
+    T2 v[NF][1][R];
 #pragma unroll
-    for (int f = 0; f < NF; ++f) {
+    for (int f = 0; f < NF; ++f)
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[f][r] = sm[fb[f] + padi<LOGE>(b + (r << lognb))];
-      bfly<LOGR, INV>(v[f], k, logNs, tw, logP);
-    }
+      for (int r = 0; r < R; ++r) v[f][0][r] = sm[fb[f] + padi<LOGE>(b + (r << lognb))];
+    bfly_shared<LOGR, INV>(v, 0, k, logNs, tw, logP);
     const int base = ((b - k) << LOGR) + k;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       T2 vals[NF];
 #pragma unroll
-      for (int f = 0; f < NF; ++f) vals[f] = v[f][r];
+      for (int f = 0; f < NF; ++f) vals[f] = v[f][0][r];
       emit(base + (r << logNs), vals);
     }
   }
@@ -258,17 +269,20 @@ __device__ __forceinline__ void conv_mid_pass(T2* __restrict__ sm, const int (&f
   const int lognb = logH - LOGR;
   T2 v[NF][NB][R];
 #pragma unroll
-  for (int f = 0; f < NF; ++f)
+  for (int t = 0; t < NB; ++t) {
+    const int b = j + t * tpf;
 #pragma unroll
-    for (int t = 0; t < NB; ++t) {
-      const int b = j + t * tpf;
+    for (int f = 0; f < NF; ++f)
 #pragma unroll
       for (int r = 0; r < R; ++r) v[f][t][r] = sm[fb[f] + padi<LOGE>(b + (r << lognb))];
-      bfly<LOGR, false>(v[f][t], b, lognb, tw, logP);   // Ns = H/R, so b mod Ns = b
+    bfly_shared<LOGR, false>(v, t, b, lognb, tw, logP);   // Ns = H/R, so b mod Ns = b
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
 #pragma unroll
       for (int r = 0; r < R; ++r) v[f][t][r] = mul(f, b + (r << lognb), v[f][t][r]);
-      dft_reg<R, true>(v[f][t]);                         // inverse pass with Ns = 1: no twiddles
+      dft_reg<R, true>(v[f][t]);                          // inverse pass with Ns = 1: no twiddles
     }
+  }
   __syncthreads();
 #pragma unroll
   for (int f = 0; f < NF; ++f)
