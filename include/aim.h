@@ -140,7 +140,8 @@ typedef struct {
 typedef struct {
   double tol;          /* relative residual target ||b - A x|| / ||b|| of the solved system */
   int restart;         /* GMRES restart length (1..10000); the Krylov basis takes
-                          (restart+4) * n * nrhs * 16 bytes of device memory */
+                          (restart+4) * n * nrhs * 16 bytes of device memory and the
+                          Hessenberg matrix about restart^2/2 * nrhs * 16 bytes */
   int max_iter;        /* total inner iterations per right-hand side */
   int precision;       /* AIM_FP64, AIM_FP64_NATIVE, or AIM_MIXED (FP32 grid inner solves inside
                           iterative refinement with AIM_FP64 residuals) */
@@ -343,7 +344,8 @@ aim_status aim_grid_product_noalloc(aim_ctx* ctx, int filtered, int nrhs, const 
                                     int precision, void* stream);
 
 /* Solves A x = b for nrhs right-hand sides by restarted GMRES with FP64 Arnoldi
- * (classical Gram-Schmidt, applied twice). `system` is AIM_OP_EFIE, AIM_OP_EFIE_ALPHA,
+ * (classical Gram-Schmidt applied twice, the second pass delayed by one step: two reads of the
+ * Krylov basis per iteration). `system` is AIM_OP_EFIE, AIM_OP_EFIE_ALPHA,
  * AIM_OP_CALDERON, AIM_OP_CALDERON_ALPHA or AIM_OP_CALDERON_ALPHA2. For the Calderon systems `rhs` is the EFIE
  * excitation E and the solver forms G^-1 S G^-1 E itself (Eq. 3). In AIM_MIXED precision
  * the inner GMRES uses the FP32 grid product and the outer loop refines with FP64

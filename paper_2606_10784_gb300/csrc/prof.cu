@@ -20,7 +20,7 @@ static const char* kKernelNames[K_COUNT] = {
     "setup_segment_pairs",
     "setup_near_entries",
     "rhs_planewave",
-    "gmres_arnoldi (CGS2 projections, norm, normalisation; timed per step)",
+    "gmres_arnoldi (DCGS2 projections and updates; timed per step)",
     "grid_multi (persistent: row passes, column pass and gathers of several contexts)",
 };
 

@@ -1,8 +1,9 @@
 // Restarted GMRES for the AIM systems (the iterative solver of Sec. I; the Calderon system of
-// Eq. 3). Arnoldi runs in FP64 on the device with classical Gram-Schmidt applied twice; the
-// small Hessenberg least-squares problem (Givens rotations) is solved on the host, one
-// device-to-host copy of the new Hessenberg column per iteration. Several right-hand sides
-// run in lock step, each with its own Krylov basis.
+// Eq. 3). Arnoldi runs in FP64 on the device with classical Gram-Schmidt applied twice, the
+// second pass delayed into the next step (DCGS2, below); the small Hessenberg least-squares
+// problem (Givens rotations) is solved on the host, one device-to-host copy of the newly final
+// Hessenberg column per iteration. Several right-hand sides run in lock step, each with its own
+// Krylov basis.
 //
 // Mixed precision: the outer loop computes r = b - A x with the FP64 grid product, an inner
 // GMRES with the FP32 grid product solves A d = r to a looser tolerance, and x += d, until
@@ -140,61 +141,6 @@ __device__ __forceinline__ void warp_sum_df(float& rh, float& rl, float& ih, flo
   }
 }
 
-// Double-float form of k_multidot_partial: part[(z J + j) nrhs + r] = sum over chunk z of
-// conj(V[j][r][i]) w[r][i], products, per-thread and block sums in double-float.
-__global__ void k_multidot_partial_df(const dfc* __restrict__ V, const dfc* __restrict__ w, int n, int nrhs, int J,
-                                      double2* __restrict__ part) {
-  const int j = blockIdx.x, r = blockIdx.y, z = blockIdx.z;
-  const int i0 = z * kDotChunk, i1 = min(n, i0 + kDotChunk);
-  const dfc* v = V + ((size_t)j * nrhs + r) * n;
-  const dfc* x = w + (size_t)r * n;
-  float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    const dfc a = v[i], b = x[i];
-    float ph, pl;
-    df_dot2<+1>(a.xh, a.xl, b.xh, b.xl, a.yh, a.yl, b.yh, b.yl, ph, pl);   // ax bx + ay by
-    df_add(rh, rl, ph, pl, rh, rl);
-    df_dot2<-1>(a.xh, a.xl, b.yh, b.yl, a.yh, a.yl, b.xh, b.xl, ph, pl);   // ax by - ay bx
-    df_add(ih, il, ph, pl, ih, il);
-  }
-  // warp and block sums in double-float as well: on this part FP64 runs at 1/64 of the FP32
-  // rate, and an FP64 shuffle tree per block cost about as much time as reading the basis
-  __shared__ float s4[32][4];
-  warp_sum_df(rh, rl, ih, il);
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    s4[wid][0] = rh;
-    s4[wid][1] = rl;
-    s4[wid][2] = ih;
-    s4[wid][3] = il;
-  }
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    rh = lane < nw ? s4[lane][0] : 0.f;
-    rl = lane < nw ? s4[lane][1] : 0.f;
-    ih = lane < nw ? s4[lane][2] : 0.f;
-    il = lane < nw ? s4[lane][3] : 0.f;
-    warp_sum_df(rh, rl, ih, il);
-    if (lane == 0) part[((size_t)z * J + j) * nrhs + r] = to_d2(rh, rl, ih, il);
-  }
-}
-
-// out[t] = sum of the chunk partials (FP64, in chunk order), and its double-float copy
-__global__ void k_multidot_finish_df(const double2* __restrict__ part, int nz, int count, double2* __restrict__ out,
-                                     dfc* __restrict__ out_df) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= count) return;
-  double re = 0.0, im = 0.0;
-  for (int z = 0; z < nz; ++z) {
-    const double2 p = part[(size_t)z * count + t];
-    re += p.x;
-    im += p.y;
-  }
-  out[t] = double2{re, im};
-  out_df[t] = to_dfc(double2{re, im});
-}
-
 // Stage 1 of the basis update: part[chunk][r][i] = sum over the chunk of V[j][r][i] c[j*nrhs + r],
 // kept in double-float (converting every chunk sum to FP64 and adding them on the FP64 pipe, at
 // 1/64 of the FP32 rate here, cost more than the additions in double-float)
@@ -240,9 +186,320 @@ __global__ void k_vcombine_finish_df(const dfc* __restrict__ part, int nchunks, 
   if (out_df != nullptr) out_df[t] = to_dfc(o);
 }
 
-__global__ void k_add_small(double2* a, const double2* b, int count) {
+// ------------------------------------------------------------------------------------
+// Arnoldi with delayed reorthogonalisation (DCGS2: classical Gram-Schmidt applied twice, the
+// second pass of step j-1 carried out in step j; Swirydowicz, Langou, Ananthan, Yang, Thomas,
+// "Low synchronization Gram-Schmidt and GMRES algorithms", 2020; Bielich et al., "Low-synch
+// Gram-Schmidt with delayed reorthogonalization for Krylov solvers", 2022).
+//
+// Step j starts from the orthonormal v_0..v_{j-1} and the candidate u for v_j (projected once,
+// not normalised), kept in basis slot j. With w = A u, one read of the basis gives
+//   s = V^H u, q = u^H u, t = V^H w, p = u^H w,
+// and then (V = [v_0..v_{j-1}], H the Hessenberg matrix, <v, v_l> = 0 used throughout):
+//   beta = sqrt(q - |s|^2),  v_j = (u - V s) / beta        (the delayed second pass of u)
+//   H[l][j-1] += s_l, H[j][j-1] = beta                     (column j-1 is now final)
+//   A v_j = (w - V (H s) - s_{j-1} (u - V s)) / beta      (A V = V H + beta v_j e_{j-1}^T)
+//   c = V^H A v_j = (t - H s) / beta,  d = v_j^H A v_j = (p - s^H t) / beta^2 - s_{j-1}
+//   u_{j+1} = A v_j - V c - v_j d = w / beta - kappa u - V g,
+//   kappa = (s_{j-1} + d) / beta,  g = H s / beta + c - kappa s,
+// so H[.][j] = (c, d) is column j's first pass, and v_j and u_{j+1} come from one more read of
+// the basis. The basis is read twice per step instead of four times.
+// ------------------------------------------------------------------------------------
+
+// Offset of Hessenberg entry (l, m), l <= m + 1, in the column-packed upper Hessenberg matrix
+// (column m holds rows 0..m+1), and the entries of a restart length's matrix
+__host__ __device__ __forceinline__ size_t hess_index(int l, int m) { return (size_t)m * (m + 3) / 2 + l; }
+__host__ __device__ __forceinline__ size_t hess_entries(int restart) { return (size_t)restart * (restart + 3) / 2; }
+
+// part0[(z J + l) nrhs + r] = sum over chunk z of conj(V[l][r][i]) R0[r][i]; part1 likewise with
+// R1 (not written when R1 is null): both projections over one read of the basis (one basis
+// vector per block: four per block, sharing the loads of R0 and R1, ran 30 % slower at 3 CTAs
+// per SM instead of 6)
+__global__ void k_multidot2_partial_df(const dfc* __restrict__ V, const dfc* __restrict__ R0, const dfc* __restrict__ R1,
+                                       int n, int nrhs, int J, double2* __restrict__ part0, double2* __restrict__ part1) {
+  const int l = blockIdx.x, r = blockIdx.y, z = blockIdx.z;
+  const int i0 = z * kDotChunk, i1 = min(n, i0 + kDotChunk);
+  const dfc* v = V + ((size_t)l * nrhs + r) * n;
+  const dfc* x0 = R0 + (size_t)r * n;
+  const dfc* x1 = R1 != nullptr ? R1 + (size_t)r * n : nullptr;
+  float a_rh = 0.f, a_rl = 0.f, a_ih = 0.f, a_il = 0.f;
+  float b_rh = 0.f, b_rl = 0.f, b_ih = 0.f, b_il = 0.f;
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const dfc a = v[i], b = x0[i];
+    float ph, pl;
+    df_dot2<+1>(a.xh, a.xl, b.xh, b.xl, a.yh, a.yl, b.yh, b.yl, ph, pl);
+    df_add(a_rh, a_rl, ph, pl, a_rh, a_rl);
+    df_dot2<-1>(a.xh, a.xl, b.yh, b.yl, a.yh, a.yl, b.xh, b.xl, ph, pl);
+    df_add(a_ih, a_il, ph, pl, a_ih, a_il);
+    if (x1 != nullptr) {
+      const dfc c = x1[i];
+      df_dot2<+1>(a.xh, a.xl, c.xh, c.xl, a.yh, a.yl, c.yh, c.yl, ph, pl);
+      df_add(b_rh, b_rl, ph, pl, b_rh, b_rl);
+      df_dot2<-1>(a.xh, a.xl, c.yh, c.yl, a.yh, a.yl, c.xh, c.xl, ph, pl);
+      df_add(b_ih, b_il, ph, pl, b_ih, b_il);
+    }
+  }
+  __shared__ float s8[32][8];
+  warp_sum_df(a_rh, a_rl, a_ih, a_il);
+  warp_sum_df(b_rh, b_rl, b_ih, b_il);
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    s8[wid][0] = a_rh; s8[wid][1] = a_rl; s8[wid][2] = a_ih; s8[wid][3] = a_il;
+    s8[wid][4] = b_rh; s8[wid][5] = b_rl; s8[wid][6] = b_ih; s8[wid][7] = b_il;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+    const bool in = lane < nw;
+    a_rh = in ? s8[lane][0] : 0.f; a_rl = in ? s8[lane][1] : 0.f; a_ih = in ? s8[lane][2] : 0.f; a_il = in ? s8[lane][3] : 0.f;
+    b_rh = in ? s8[lane][4] : 0.f; b_rl = in ? s8[lane][5] : 0.f; b_ih = in ? s8[lane][6] : 0.f; b_il = in ? s8[lane][7] : 0.f;
+    warp_sum_df(a_rh, a_rl, a_ih, a_il);
+    warp_sum_df(b_rh, b_rl, b_ih, b_il);
+    if (lane == 0) {
+      const size_t o = ((size_t)z * J + l) * nrhs + r;
+      part0[o] = to_d2(a_rh, a_rl, a_ih, a_il);
+      if (part1 != nullptr) part1[o] = to_d2(b_rh, b_rl, b_ih, b_il);
+    }
+  }
+}
+
+// D0[l nrhs + r], D1[...] = chunk sums in chunk order (FP64), D0's double-float copy, and the
+// delayed second pass of column j-1: H[l][j-1] += s_l = D0[l] for l < j
+__global__ void k_dcgs2_finish(const double2* __restrict__ part0, const double2* __restrict__ part1, int nz, int J,
+                               int nrhs, int j, int restart, double2* __restrict__ D0, double2* __restrict__ D1,
+                               dfc* __restrict__ D0df, dfc* __restrict__ H) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < count) { a[t].x += b[t].x; a[t].y += b[t].y; }
+  const int count = J * nrhs;
+  if (t >= count) return;
+  double re = 0.0, im = 0.0, re1 = 0.0, im1 = 0.0;
+#pragma unroll 5
+  for (int z = 0; z < nz; ++z) {
+    const double2 a = part0[(size_t)z * count + t];
+    re += a.x;
+    im += a.y;
+    if (part1 != nullptr) {
+      const double2 b = part1[(size_t)z * count + t];
+      re1 += b.x;
+      im1 += b.y;
+    }
+  }
+  D0[t] = double2{re, im};
+  if (part1 != nullptr) D1[t] = double2{re1, im1};
+  const dfc sd = to_dfc(double2{re, im});
+  D0df[t] = sd;
+  const int l = t / nrhs, r = t - l * nrhs;
+  if (j >= 1 && l < j) {
+    dfc& h = H[(size_t)r * hess_entries(restart) + hess_index(l, j - 1)];
+    dfc o;
+    df_add(h.xh, h.xl, sd.xh, sd.xl, o.xh, o.xl);
+    df_add(h.yh, h.yl, sd.yh, sd.yl, o.yh, o.yl);
+    h = o;
+  }
+}
+
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) { return double2{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ __forceinline__ double2 zconjmul(double2 a, double2 b) { return double2{a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x}; }
+
+// Block sum (fixed tree) of three values over the threads of a block; every thread gets it
+__device__ __forceinline__ void block_sum3(double& a, double& b, double& c, double (*sh)[3]) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, off);
+    b += __shfl_xor_sync(0xffffffffu, b, off);
+    c += __shfl_xor_sync(0xffffffffu, c, off);
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) { sh[wid][0] = a; sh[wid][1] = b; sh[wid][2] = c; }
+  __syncthreads();
+  const int nw = blockDim.x >> 5;
+  a = b = c = 0.0;
+  for (int w = 0; w < nw; ++w) { a += sh[w][0]; b += sh[w][1]; c += sh[w][2]; }
+}
+
+// Blocks x < ceil(j/8): hs[l nrhs + r] = (H s)_l = sum_{m >= l-1} H[l][m] s_m for 8 rows l each
+// (double-float; 32 slices of m per row, added in slice order). H s is small next to t (s is the
+// second pass's correction), so its rounding matters less than that of t.
+// Block x = ceil(j/8): the step's scalars for rhs r: beta = sqrt(q - |s|^2) (colout row j and
+// H[j][j-1]), and unless final_step d = (p - s^H t)/beta^2 - s_{j-1}, kappa = (s_{j-1} + d)/beta,
+// into scal = (1/beta, kappa, d).
+constexpr int kHsRows = 8, kHsSlices = 32;
+
+__global__ void __launch_bounds__(256) k_dcgs2_hs_scal(const dfc* H, const dfc* __restrict__ sdf,
+                                                       const double2* __restrict__ D0, const double2* __restrict__ D1,
+                                                       const int* __restrict__ active, int j, int nrhs, int restart,
+                                                       int final_step, double2* __restrict__ hs,
+                                                       double2* __restrict__ colout, dfc* Hw,
+                                                       double2* __restrict__ scal) {
+  const int r = blockIdx.y;
+  const int nrow_blocks = final_step ? 0 : (j + kHsRows - 1) / kHsRows;
+  const size_t hb = (size_t)r * hess_entries(restart);
+  if ((int)blockIdx.x < nrow_blocks) {
+    const int rl = threadIdx.x % kHsRows, sl = threadIdx.x / kHsRows;
+    const int l0 = blockIdx.x * kHsRows, l = l0 + rl;
+    float rh = 0.f, rlo = 0.f, ih = 0.f, il = 0.f;
+#pragma unroll 4
+    for (int m = max(l0 - 1, 0) + sl; m < j; m += kHsSlices) {
+      if (l < j && l <= m + 1) {
+        const dfc a = H[hb + hess_index(l, m)], b = sdf[(size_t)m * nrhs + r];
+        float ph, pl;
+        df_dot2<-1>(a.xh, a.xl, b.xh, b.xl, a.yh, a.yl, b.yh, b.yl, ph, pl);
+        df_add(rh, rlo, ph, pl, rh, rlo);
+        df_dot2<+1>(a.xh, a.xl, b.yh, b.yl, a.yh, a.yl, b.xh, b.xl, ph, pl);
+        df_add(ih, il, ph, pl, ih, il);
+      }
+    }
+    __shared__ float part[kHsSlices][kHsRows][4];
+    part[sl][rl][0] = rh;
+    part[sl][rl][1] = rlo;
+    part[sl][rl][2] = ih;
+    part[sl][rl][3] = il;
+    __syncthreads();
+    if (sl == 0 && l < j) {
+      for (int k = 1; k < kHsSlices; ++k) {
+        df_add(rh, rlo, part[k][rl][0], part[k][rl][1], rh, rlo);
+        df_add(ih, il, part[k][rl][2], part[k][rl][3], ih, il);
+      }
+      hs[(size_t)l * nrhs + r] = to_d2(rh, rlo, ih, il);
+    }
+    return;
+  }
+  __shared__ double sh[32][3];
+  double ss = 0.0, st_re = 0.0, st_im = 0.0;
+  for (int l = threadIdx.x; l < j; l += blockDim.x) {
+    const double2 sv = D0[(size_t)l * nrhs + r];
+    ss += sv.x * sv.x + sv.y * sv.y;
+    if (!final_step) {
+      const double2 c = zconjmul(sv, D1[(size_t)l * nrhs + r]);
+      st_re += c.x;
+      st_im += c.y;
+    }
+  }
+  block_sum3(ss, st_re, st_im, sh);
+  if (threadIdx.x != 0) return;
+  const double q = D0[(size_t)j * nrhs + r].x;
+  const double b2 = q - ss;
+  // a non-finite value reaches the host through beta (the norm it checks); b2 <= 0 is a breakdown
+  const double beta = !active[r] ? 0.0 : !isfinite(b2) ? b2 : b2 > 0.0 ? sqrt(b2) : 0.0;
+  const double ib = beta > 0.0 ? 1.0 / beta : 0.0;
+  if (j >= 1) {
+    colout[(size_t)j * nrhs + r] = double2{beta, 0.0};
+    Hw[hb + hess_index(j, j - 1)] = to_dfc(double2{beta, 0.0});
+  }
+  if (final_step) return;
+  const double2 p = D1[(size_t)j * nrhs + r];
+  const double2 slast = j >= 1 ? D0[(size_t)(j - 1) * nrhs + r] : double2{0.0, 0.0};
+  double2 d = double2{(p.x - st_re) * ib * ib - slast.x, (p.y - st_im) * ib * ib - slast.y};
+  if (beta == 0.0) d = double2{0.0, 0.0};
+  const double2 kappa = double2{(slast.x + d.x) * ib, (slast.y + d.y) * ib};
+  scal[r] = double2{ib, 0.0};
+  scal[nrhs + r] = kappa;
+  scal[2 * nrhs + r] = d;
+  Hw[hb + hess_index(j, j)] = to_dfc(d);
+}
+
+// Per entry l < j of rhs r (t = l nrhs + r): the final column j-1 for the host (colout, from H
+// after the delayed pass), and unless final_step c_l = (t_l - (H s)_l)/beta into H[l][j],
+// g_l = (H s)_l / beta + c_l - kappa s_l and a1_l = s_l / beta (double-float, for the updates)
+__global__ void k_dcgs2_coeffs(const double2* __restrict__ D0, const double2* __restrict__ D1,
+                               const double2* __restrict__ hs, const double2* __restrict__ scal, int j, int nrhs,
+                               int restart, int final_step, dfc* __restrict__ H, double2* __restrict__ colout,
+                               dfc* __restrict__ a1, dfc* __restrict__ g) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= j * nrhs) return;
+  const int l = t / nrhs, r = t - l * nrhs;
+  const size_t hb = (size_t)r * hess_entries(restart);
+  if (j >= 1) {
+    const dfc h = H[hb + hess_index(l, j - 1)];
+    colout[t] = to_d2(h.xh, h.xl, h.yh, h.yl);
+  }
+  if (final_step) return;
+  const double ib = scal[r].x;
+  const double2 kappa = scal[nrhs + r];
+  const double2 sv = D0[t], tv = D1[t], hv = hs[t];
+  const double2 c = double2{(tv.x - hv.x) * ib, (tv.y - hv.y) * ib};
+  const double2 ks = zmul(kappa, sv);
+  g[t] = to_dfc(double2{hv.x * ib + c.x - ks.x, hv.y * ib + c.y - ks.y});
+  a1[t] = to_dfc(double2{sv.x * ib, sv.y * ib});
+  H[hb + hess_index(l, j)] = to_dfc(c);
+}
+
+// Stage 1 of the two updates of a step, over one read of the basis: part1[chunk][r][i] =
+// sum over the chunk of V[l][r][i] a1[l], part2 the same with g
+__global__ void k_vcombine2_partial_df(const dfc* __restrict__ V, const dfc* __restrict__ a1, const dfc* __restrict__ g,
+                                       int J, int n, int nrhs, dfc* __restrict__ part1, dfc* __restrict__ part2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int chunk = blockIdx.y, r = blockIdx.z;
+  if (i >= n) return;
+  const int j0 = chunk * kCgsChunk, j1 = min(J, j0 + kCgsChunk);
+  float a_rh = 0.f, a_rl = 0.f, a_ih = 0.f, a_il = 0.f;
+  float b_rh = 0.f, b_rl = 0.f, b_ih = 0.f, b_il = 0.f;
+#pragma unroll 4
+  for (int l = j0; l < j1; ++l) {
+    const dfc v = V[((size_t)l * nrhs + r) * n + i];
+    const dfc h = a1[(size_t)l * nrhs + r], k = g[(size_t)l * nrhs + r];
+    float ph, pl;
+    df_dot2<-1>(v.xh, v.xl, h.xh, h.xl, v.yh, v.yl, h.yh, h.yl, ph, pl);
+    df_add(a_rh, a_rl, ph, pl, a_rh, a_rl);
+    df_dot2<+1>(v.xh, v.xl, h.yh, h.yl, v.yh, v.yl, h.xh, h.xl, ph, pl);
+    df_add(a_ih, a_il, ph, pl, a_ih, a_il);
+    df_dot2<-1>(v.xh, v.xl, k.xh, k.xl, v.yh, v.yl, k.yh, k.yl, ph, pl);
+    df_add(b_rh, b_rl, ph, pl, b_rh, b_rl);
+    df_dot2<+1>(v.xh, v.xl, k.yh, k.yl, v.yh, v.yl, k.xh, k.xl, ph, pl);
+    df_add(b_ih, b_il, ph, pl, b_ih, b_il);
+  }
+  const size_t o = ((size_t)chunk * nrhs + r) * n + i;
+  part1[o] = dfc{a_rh, a_rl, a_ih, a_il};
+  part2[o] = dfc{b_rh, b_rl, b_ih, b_il};
+}
+
+// Stage 2: v_j = u / beta - V a1 into slot j (u is read there first), u_{j+1} = w / beta - kappa u -
+// V g into slot j+1 and, in binary64, into cur (the next product's input). Four adjacent threads
+// per element sum every fourth chunk; a fixed shuffle tree adds their sums.
+constexpr int kFinishLanes = 4;
+
+__global__ void k_vcombine2_finish_df(const dfc* __restrict__ part1, const dfc* __restrict__ part2, int nchunks, int n,
+                                      int nrhs, const double2* __restrict__ scal, dfc* __restrict__ Vj,
+                                      const double2* __restrict__ w, dfc* __restrict__ Vnext, double2* __restrict__ cur) {
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = (int)(gt / kFinishLanes), q = (int)(gt % kFinishLanes);
+  const bool live = t < n * nrhs;   // whole groups of four: the shuffles below need every lane
+  float a_rh = 0.f, a_rl = 0.f, a_ih = 0.f, a_il = 0.f;
+  float b_rh = 0.f, b_rl = 0.f, b_ih = 0.f, b_il = 0.f;
+  if (live) {
+#pragma unroll 2
+    for (int ch = q; ch < nchunks; ch += kFinishLanes) {
+      const dfc p = part1[(size_t)ch * n * nrhs + t], pp = part2[(size_t)ch * n * nrhs + t];
+      df_add(a_rh, a_rl, p.xh, p.xl, a_rh, a_rl);
+      df_add(a_ih, a_il, p.yh, p.yl, a_ih, a_il);
+      df_add(b_rh, b_rl, pp.xh, pp.xl, b_rh, b_rl);
+      df_add(b_ih, b_il, pp.yh, pp.yl, b_ih, b_il);
+    }
+  }
+#pragma unroll
+  for (int off = 1; off < kFinishLanes; off <<= 1) {
+    const float o0 = __shfl_xor_sync(0xffffffffu, a_rh, off), o1 = __shfl_xor_sync(0xffffffffu, a_rl, off);
+    const float o2 = __shfl_xor_sync(0xffffffffu, a_ih, off), o3 = __shfl_xor_sync(0xffffffffu, a_il, off);
+    const float o4 = __shfl_xor_sync(0xffffffffu, b_rh, off), o5 = __shfl_xor_sync(0xffffffffu, b_rl, off);
+    const float o6 = __shfl_xor_sync(0xffffffffu, b_ih, off), o7 = __shfl_xor_sync(0xffffffffu, b_il, off);
+    df_add(a_rh, a_rl, o0, o1, a_rh, a_rl);
+    df_add(a_ih, a_il, o2, o3, a_ih, a_il);
+    df_add(b_rh, b_rl, o4, o5, b_rh, b_rl);
+    df_add(b_ih, b_il, o6, o7, b_ih, b_il);
+  }
+  if (!live || q != 0) return;
+  const int r = t / n;
+  const double2 P1 = to_d2(a_rh, a_rl, a_ih, a_il), P2 = to_d2(b_rh, b_rl, b_ih, b_il);
+  const double ib = scal[r].x;
+  const double2 kappa = scal[nrhs + r];
+  const dfc ud = Vj[t];
+  const double2 u = to_d2(ud.xh, ud.xl, ud.yh, ud.yl);
+  const double2 wv = w[t];
+  const double2 vj = double2{u.x * ib - P1.x, u.y * ib - P1.y};
+  const double2 ku = zmul(kappa, u);
+  const double2 un = double2{wv.x * ib - ku.x - P2.x, wv.y * ib - ku.y - P2.y};
+  Vj[t] = to_dfc(vj);
+  Vnext[t] = to_dfc(un);
+  cur[t] = un;
 }
 
 // v = w[r] / sqrt(nrm2[r].x) (zero if the norm vanished, or active[r] == 0): the new basis
@@ -284,6 +541,11 @@ struct Workspace {
   double2 *w, *r, *cur, *tmp, *dots, *dots2, *nrm;
   dfc *wdf, *dots_df, *dots2_df;
   int* active;
+  // delayed reorthogonalisation: Hessenberg matrix (row-packed, per rhs), H s, the final column
+  // staged for the host, the update coefficients and the two scalars (1/beta, kappa) per rhs
+  dfc* H;
+  double2 *hs, *colout, *scal;
+  dfc* g;
 };
 
 inline int blocks_for(long long total, int tpb) { return (int)((total + tpb - 1) / tpb); }
@@ -368,17 +630,6 @@ struct OpGraph {
   }
 };
 
-// out[j*nrhs + r] = <V[j][r], w[r]> for j < J over the double-float basis (two launches)
-static aim_status multidot_df(const dfc* V, const dfc* w, int J, int n, int nrhs, double2* out, dfc* out_df,
-                              double2* part, cudaStream_t st) {
-  const int nz = (n + kDotChunk - 1) / kDotChunk;
-  count_launches(K_GMRES, 2);
-  k_multidot_partial_df<<<dim3(J, nrhs, nz), 256, 0, st>>>(V, w, n, nrhs, J, part);
-  k_multidot_finish_df<<<blocks_for((long long)J * nrhs, 256), 256, 0, st>>>(part, nz, J * nrhs, out, out_df);
-  AIM_CUDA_TRY(cudaGetLastError());
-  return AIM_OK;
-}
-
 // out += sign * V c over J vectors of the double-float basis (two launches, deterministic order)
 static void vcombine_df(const dfc* V, const dfc* c, int J, int n, int nrhs, double sign, double2* out, dfc* out_df,
                         double2* part, cudaStream_t st) {
@@ -390,18 +641,21 @@ static void vcombine_df(const dfc* V, const dfc* c, int J, int n, int nrhs, doub
 }
 
 size_t krylov_bytes(size_t n, int nrhs, int restart) {
-  // partial sums of the basis updates (chunks of kCgsChunk vectors) or of the inner products
-  // (chunks of kDotChunk elements), whichever needs more
+  // partial sums of the two basis updates of a step (chunks of kCgsChunk vectors) or of its two
+  // sets of inner products (chunks of kDotChunk elements), whichever needs more
   const size_t nz = (n + kDotChunk - 1) / kDotChunk;
-  const size_t part_vecs = std::max((size_t)(restart + kCgsChunk) / kCgsChunk, (nz * (restart + 1) + n - 1) / n);
+  const size_t part_vecs =
+      std::max(2 * ((size_t)(restart + kCgsChunk) / kCgsChunk), (2 * nz * (restart + 1) + n - 1) / n);
   // basis (restart + 1, double-float), w, r, the current vector, w in double-float, partial sums
   const size_t nvec = (size_t)(restart + 1) + 4 + part_vecs;
-  return nvec * nrhs * n * sizeof(double2);
+  // and the Hessenberg matrix of each right-hand side (double-float, row-packed)
+  return nvec * nrhs * n * sizeof(double2) + (size_t)nrhs * hess_entries(restart) * sizeof(dfc);
 }
 
 size_t reduction_bytes(int nrhs, int restart) {
-  // dots, dots2, norms, their double-float copies, and the active flags
-  return ((size_t)(restart + 2) * 5 + 1) * nrhs * sizeof(double2) + nrhs * sizeof(int);
+  // dots, dots2, norms, double-float copies, H s, the staged column, g, the step scalars, and
+  // the active flags
+  return ((size_t)(restart + 2) * 8 + 3) * nrhs * sizeof(double2) + nrhs * sizeof(int);
 }
 
 static aim_status ensure_krylov(aim_ctx* ctx, int nrhs, int restart) {
@@ -460,7 +714,17 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
   ws.nrm = red + (size_t)(restart + 2) * 2 * nrhs; // nrhs
   ws.dots_df = reinterpret_cast<dfc*>(red + (size_t)(restart + 2) * 3 * nrhs);   // (restart+1) * nrhs
   ws.dots2_df = reinterpret_cast<dfc*>(red + (size_t)(restart + 2) * 4 * nrhs);  // (restart+1) * nrhs
-  ws.active = reinterpret_cast<int*>(red + ((size_t)(restart + 2) * 5 + 1) * nrhs);
+  ws.hs = red + (size_t)(restart + 2) * 5 * nrhs;                                  // (restart+1) * nrhs
+  ws.colout = red + (size_t)(restart + 2) * 6 * nrhs;                              // (restart+2) * nrhs
+  ws.g = reinterpret_cast<dfc*>(red + (size_t)(restart + 2) * 7 * nrhs);           // (restart+1) * nrhs
+  ws.scal = red + (size_t)(restart + 2) * 8 * nrhs;                                // 2 * nrhs
+  ws.active = reinterpret_cast<int*>(red + ((size_t)(restart + 2) * 8 + 3) * nrhs);
+  {
+    const size_t nz = ((size_t)n + kDotChunk - 1) / kDotChunk;
+    const size_t part_vecs =
+        std::max(2 * ((size_t)(restart + kCgsChunk) / kCgsChunk), (2 * nz * (restart + 1) + n - 1) / n);
+    ws.H = reinterpret_cast<dfc*>(ws.tmp + part_vecs * vsz);
+  }
   double2* hred = reinterpret_cast<double2*>(ctx->red_host);
   const int tpb = 256;
   const int nb = blocks_for((long long)vsz, tpb);
@@ -519,42 +783,78 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
       for (int j = 1; j <= restart; ++j) g[(size_t)j * nrhs + r] = {0.0, 0.0};
       jconv[r] = 0;
     }
-    // Arnoldi step j: w = A v_j, CGS2 against v_0..v_j, v_{j+1} = w / ||w||, and the D2H copy
-    // of Hessenberg column j into host slot j % 2. A step needs nothing from the host, so step
-    // j + 1 is queued before the host waits for column j: the Givens updates on the host overlap
-    // the next matvec on the device (one step of lookahead; the step queued after the last
-    // useful one is discarded).
+    // Arnoldi step j (delayed reorthogonalisation, see the kernels above): w = A u_j, both sets of
+    // projections over one read of the basis, the coefficients, and v_j and u_{j+1} from one more
+    // read; step j (j >= 1) finalises Hessenberg column j - 1 and copies it to host slot
+    // (j - 1) % 2. Step `restart` only finalises the last column (no product). A step needs
+    // nothing from the host, so steps c + 1 and c + 2 are queued before the host waits for column
+    // c: the Givens updates overlap the device work, and at most two queued steps are discarded
+    // when a cycle ends early (they write only basis slots and columns past the ones in use).
     auto arnoldi_step = [&](int j) -> aim_status {
-      double2* slot = hred + (size_t)(j & 1) * (restart + 2) * nrhs;
-      // w = A v_j (cur = v_j)
-      if (!op_graph.tried) op_graph.capture(ctx, op, nrhs, ws.cur, ws.w, precision, st);
-      if (op_graph.exec != nullptr) {
-        AIM_TRY(op_graph.replay(st));
-      } else {
-        AIM_TRY(solver_apply(ctx, op, nrhs, ws.cur, ws.w, precision, st));
+      const bool final_step = j == restart;
+      dfc* Vj = ws.V + (size_t)j * vsz;
+      if (!final_step) {
+        // w = A u_j (cur = u_j)
+        if (!op_graph.tried) op_graph.capture(ctx, op, nrhs, ws.cur, ws.w, precision, st);
+        if (op_graph.exec != nullptr) {
+          AIM_TRY(op_graph.replay(st));
+        } else {
+          AIM_TRY(solver_apply(ctx, op, nrhs, ws.cur, ws.w, precision, st));
+        }
       }
-      // CGS2 (3 launches here + 2 x 2 in multidot_df + 2 x 2 in vcombine_df + 2 in dot_norms),
-      // timed as one group when profiling
+      // 7 launches (4 in the final step), timed as one group when profiling
       ProfScope group(K_GMRES, st, /*count_launch=*/false);
+      const int J = j + 1;   // v_0..v_{j-1} and the candidate u_j in slot j
+      const int nz = (n + kDotChunk - 1) / kDotChunk;
+      double2* part0 = ws.tmp;
+      double2* part1 = ws.tmp + (size_t)nz * J * nrhs;
+      if (!final_step) {
+        count_launches(K_GMRES, 1);
+        k_to_dfc<<<nb, tpb, 0, st>>>(ws.w, (int)vsz, ws.wdf);
+      }
       count_launches(K_GMRES, 3);
-      k_to_dfc<<<nb, tpb, 0, st>>>(ws.w, (int)vsz, ws.wdf);
-      AIM_TRY(multidot_df(ws.V, ws.wdf, j + 1, n, nrhs, ws.dots, ws.dots_df, ws.tmp, st));
-      vcombine_df(ws.V, ws.dots_df, j + 1, n, nrhs, -1.0, ws.w, ws.wdf, ws.tmp, st);
-      AIM_TRY(multidot_df(ws.V, ws.wdf, j + 1, n, nrhs, ws.dots2, ws.dots2_df, ws.tmp, st));
-      vcombine_df(ws.V, ws.dots2_df, j + 1, n, nrhs, -1.0, ws.w, nullptr, ws.tmp, st);
-      k_add_small<<<blocks_for((j + 1) * nrhs, tpb), tpb, 0, st>>>(ws.dots, ws.dots2, (j + 1) * nrhs);
-      AIM_TRY(dot_norms(ws.w, n, nrhs, ws.nrm, ws.tmp, st));
-      k_normalize<<<nb, tpb, 0, st>>>(ws.w, ws.nrm, ws.active, n, nrhs, ws.V + (size_t)(j + 1) * vsz, ws.cur);
+      k_multidot2_partial_df<<<dim3(J, nrhs, nz), 256, 0, st>>>(
+          ws.V, Vj, final_step ? nullptr : ws.wdf, n, nrhs, J, part0, final_step ? nullptr : part1);
+      k_dcgs2_finish<<<blocks_for((long long)J * nrhs, tpb), tpb, 0, st>>>(part0, final_step ? nullptr : part1, nz, J,
+                                                                          nrhs, j, restart, ws.dots, ws.dots2,
+                                                                          ws.dots_df, ws.H);
+      const int hs_blocks = final_step ? 0 : (j + kHsRows - 1) / kHsRows;
+      k_dcgs2_hs_scal<<<dim3(hs_blocks + 1, nrhs), 256, 0, st>>>(ws.H, ws.dots_df, ws.dots, ws.dots2, ws.active, j, nrhs,
+                                                                 restart, final_step ? 1 : 0, ws.hs, ws.colout, ws.H,
+                                                                 ws.scal);
+      if (j >= 1) {
+        count_launches(K_GMRES, 1);
+        k_dcgs2_coeffs<<<blocks_for((long long)j * nrhs, tpb), tpb, 0, st>>>(ws.dots, ws.dots2, ws.hs, ws.scal, j, nrhs,
+                                                                             restart, final_step ? 1 : 0, ws.H,
+                                                                             ws.colout, ws.dots2_df, ws.g);
+      }
+      if (!final_step) {
+        const int nch = (j + kCgsChunk - 1) / kCgsChunk;
+        dfc* p1 = reinterpret_cast<dfc*>(ws.tmp);
+        dfc* p2 = p1 + (size_t)nch * vsz;
+        if (nch > 0) {
+          count_launches(K_GMRES, 1);
+          k_vcombine2_partial_df<<<dim3((n + 255) / 256, nch, nrhs), 256, 0, st>>>(ws.V, ws.dots2_df, ws.g, j, n, nrhs,
+                                                                                   p1, p2);
+        }
+        count_launches(K_GMRES, 1);
+        k_vcombine2_finish_df<<<blocks_for((long long)vsz * kFinishLanes, tpb), tpb, 0, st>>>(p1, p2, nch, n, nrhs, ws.scal,
+                                                                                             Vj, ws.w, Vj + vsz, ws.cur);
+      }
       AIM_CUDA_TRY(cudaGetLastError());
-      AIM_CUDA_TRY(cudaMemcpyAsync(slot, ws.dots, (size_t)(j + 1) * nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
-      AIM_CUDA_TRY(cudaMemcpyAsync(slot + (size_t)(j + 1) * nrhs, ws.nrm, nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
-      AIM_CUDA_TRY(cudaEventRecord(col_ready.e[j & 1], st));
+      if (j >= 1) {
+        double2* slot = hred + (size_t)((j - 1) & 1) * (restart + 2) * nrhs;
+        AIM_CUDA_TRY(cudaMemcpyAsync(slot, ws.colout, (size_t)(j + 1) * nrhs * sizeof(double2), cudaMemcpyDeviceToHost, st));
+        AIM_CUDA_TRY(cudaEventRecord(col_ready.e[(j - 1) & 1], st));
+      }
       return AIM_OK;
     };
     int jdone = 0;
     AIM_TRY(arnoldi_step(0));
+    AIM_TRY(arnoldi_step(1));
     for (int j = 0; j < restart; ++j) {
-      if (j + 1 < restart) AIM_TRY(arnoldi_step(j + 1));
+      // column j is finalised by step j + 1, already queued
+      if (j + 2 <= restart) AIM_TRY(arnoldi_step(j + 2));
       AIM_CUDA_TRY(cudaEventSynchronize(col_ready.e[j & 1]));
       const double2* hcol = hred + (size_t)(j & 1) * (restart + 2) * nrhs;
       jdone = j + 1;
@@ -564,8 +864,12 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
       Zc* col = Hcol[j].data();   // column j, rows 0..j+1
       for (int r = 0; r < nrhs; ++r) {
         if (!active[r] || jconv[r]) continue;
-        for (int i = 0; i <= j; ++i) col[(size_t)i * nrhs + r] = {hcol[(size_t)i * nrhs + r].x, hcol[(size_t)i * nrhs + r].y};
-        const double hn = std::sqrt(std::fmax(hcol[(size_t)(j + 1) * nrhs + r].x, 0.0));
+        for (int i = 0; i <= j; ++i) {
+          const double2 h = hcol[(size_t)i * nrhs + r];
+          if (!std::isfinite(h.x) || !std::isfinite(h.y)) return fail(AIM_ENUMERIC, "non-finite Hessenberg entry");
+          col[(size_t)i * nrhs + r] = {h.x, h.y};
+        }
+        const double hn = hcol[(size_t)(j + 1) * nrhs + r].x;
         if (!std::isfinite(hn)) return fail(AIM_ENUMERIC, "non-finite Arnoldi norm");
         col[(size_t)(j + 1) * nrhs + r] = {hn, 0.0};
         for (int i = 0; i < j; ++i) {

@@ -361,7 +361,7 @@ def test_every_feasible_schedule_gives_identical_results(te_pair, aimlib, precis
 def test_gpu_gmres_takes_the_oracle_gmres_iteration_count(te_pair):
     # the CPU baseline extrapolates the oracle's solve from its product time and the GPU solve's
     # iteration count: that rests on both GMRES taking the same number of iterations on the same
-    # system and tolerance (CGS2 on the GPU, MGS in the oracle: the same Krylov space)
+    # system and tolerance (DCGS2 on the GPU, MGS in the oracle: the same Krylov space)
     nodes, ctx, ref = te_pair
     E = dense.te_rhs(nodes, K, 0.0)
     b = ref.gram_solve(ref.S_alpha(ref.gram_solve(E)))
