@@ -314,7 +314,7 @@ aim_status upload_twiddles(aim_ctx* ctx, const double* tw2, cudaStream_t st) {
     const float ch = (float)c, sh = (float)s;
     tw[t] = double2{c, s};
     twf[t] = float2{ch, sh};
-    twdf[t] = float4{ch, (float)(c - (double)ch), sh, (float)(s - (double)sh)};
+    twdf[t] = float4{ch, sh, (float)(c - (double)ch), (float)(s - (double)sh)};   // (xh, yh, xl, yl)
   }
   AIM_TRY(upload(ctx, &ctx->tw, tw, st));
   AIM_TRY(upload(ctx, &ctx->twf, twf, st));

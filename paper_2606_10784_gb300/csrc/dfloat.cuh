@@ -14,8 +14,12 @@
 
 namespace aim {
 
+// Laid out as (xh, yh, xl, yl): the high parts and the low parts of re and im are register pairs,
+// so the complex sums and products below run the real and imaginary parts' identical operation
+// sequences as paired FP32 instructions (__fadd2_rn, __fmul2_rn, __ffma2_rn: one instruction for
+// two lanes of the same operation, each component rounded exactly as its scalar form).
 struct __align__(16) dfc {
-  float xh, xl, yh, yl;   // re = xh + xl, im = yh + yl
+  float xh, yh, xl, yl;   // re = xh + xl, im = yh + yl
 };
 
 __device__ __forceinline__ void ef_two_sum(float a, float b, float& s, float& e) {
@@ -56,38 +60,81 @@ __device__ __forceinline__ void df_dot2(float ah, float al, float bh, float bl, 
   rl = err;
 }
 
+// ---- paired forms: lane 0 carries the real part's operation, lane 1 the imaginary part's
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 f2neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) { return __fadd2_rn(a, f2neg(b)); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// df_add on both lanes: (ah + al) + (bh + bl), TwoSum of the high parts, unnormalised
+__device__ __forceinline__ void df_add2(float2 ah, float2 al, float2 bh, float2 bl, float2& rh, float2& rl) {
+  const float2 s = f2add(ah, bh);
+  const float2 bb = f2sub(s, ah);
+  const float2 e = f2add(f2sub(ah, f2sub(s, bb)), f2sub(bh, bb));
+  rh = s;
+  rl = f2add(e, f2add(al, bl));
+}
+
+// df_dot2 on both lanes: (ah + al)(bh + bl) + (ch + cl)(dh + dl), the signs folded into c by the
+// caller (lane by lane the same operations as df_dot2)
+__device__ __forceinline__ void df_dot2_2(float2 ah, float2 al, float2 bh, float2 bl, float2 ch, float2 cl, float2 dh,
+                                          float2 dl, float2& rh, float2& rl) {
+  const float2 p1 = f2mul(ah, bh);
+  const float2 e1 = f2fma(ah, bh, f2neg(p1));
+  const float2 p2 = f2mul(ch, dh);
+  const float2 e2 = f2fma(ch, dh, f2neg(p2));
+  const float2 s = f2add(p1, p2);
+  const float2 bb = f2sub(s, p1);
+  const float2 es = f2add(f2sub(p1, f2sub(s, bb)), f2sub(p2, bb));
+  float2 err = f2add(es, f2add(e1, e2));
+  err = f2fma(ah, bl, err);
+  err = f2fma(al, bh, err);
+  err = f2fma(ch, dl, err);
+  err = f2fma(cl, dh, err);
+  rh = s;
+  rl = err;
+}
+
 __device__ __forceinline__ dfc cadd(dfc a, dfc b) {
-  dfc r;
-  df_add(a.xh, a.xl, b.xh, b.xl, r.xh, r.xl);
-  df_add(a.yh, a.yl, b.yh, b.yl, r.yh, r.yl);
-  return r;
+  float2 rh, rl;
+  df_add2(f2(a.xh, a.yh), f2(a.xl, a.yl), f2(b.xh, b.yh), f2(b.xl, b.yl), rh, rl);
+  return dfc{rh.x, rh.y, rl.x, rl.y};
 }
 
 __device__ __forceinline__ dfc csub(dfc a, dfc b) {
-  dfc r;
-  df_add(a.xh, a.xl, -b.xh, -b.xl, r.xh, r.xl);
-  df_add(a.yh, a.yl, -b.yh, -b.yl, r.yh, r.yl);
-  return r;
+  float2 rh, rl;
+  df_add2(f2(a.xh, a.yh), f2(a.xl, a.yl), f2(-b.xh, -b.yh), f2(-b.xl, -b.yl), rh, rl);
+  return dfc{rh.x, rh.y, rl.x, rl.y};
 }
 
-// (x + iy)(u + iv) = (xu - yv) + i(xv + yu)
+// (x + iy)(u + iv) = (xu - yv) + i(xv + yu): lane 0 x u + (-y) v, lane 1 x v + y u
 __device__ __forceinline__ dfc cmul(dfc a, dfc b) {
-  dfc r;
-  df_dot2<-1>(a.xh, a.xl, b.xh, b.xl, a.yh, a.yl, b.yh, b.yl, r.xh, r.xl);
-  df_dot2<+1>(a.xh, a.xl, b.yh, b.yl, a.yh, a.yl, b.xh, b.xl, r.yh, r.yl);
-  return r;
+  float2 rh, rl;
+  df_dot2_2(f2(a.xh, a.xh), f2(a.xl, a.xl), f2(b.xh, b.yh), f2(b.xl, b.yl), f2(-a.yh, a.yh), f2(-a.yl, a.yl),
+            f2(b.yh, b.xh), f2(b.yl, b.xl), rh, rl);
+  return dfc{rh.x, rh.y, rl.x, rl.y};
 }
 
-// a * conj(b) = (xu + yv) + i(yu - xv)
+// a * conj(b) = (xu + yv) + i(yu - xv): lane 0 x u + y v, lane 1 y u + (-x) v
 __device__ __forceinline__ dfc cmulc(dfc a, dfc b) {
-  dfc r;
-  df_dot2<+1>(a.xh, a.xl, b.xh, b.xl, a.yh, a.yl, b.yh, b.yl, r.xh, r.xl);
-  df_dot2<-1>(a.yh, a.yl, b.xh, b.xl, a.xh, a.xl, b.yh, b.yl, r.yh, r.yl);
-  return r;
+  float2 rh, rl;
+  df_dot2_2(f2(a.xh, a.yh), f2(a.xl, a.yl), f2(b.xh, b.xh), f2(b.xl, b.xl), f2(a.yh, -a.xh), f2(a.yl, -a.xl),
+            f2(b.yh, b.yh), f2(b.yl, b.yl), rh, rl);
+  return dfc{rh.x, rh.y, rl.x, rl.y};
 }
 
-__device__ __forceinline__ dfc mul_minus_i(dfc a) { return dfc{a.yh, a.yl, -a.xh, -a.xl}; }
-__device__ __forceinline__ dfc mul_plus_i(dfc a) { return dfc{-a.yh, -a.yl, a.xh, a.xl}; }
+__device__ __forceinline__ dfc mul_minus_i(dfc a) {
+  dfc r;
+  r.xh = a.yh; r.xl = a.yl; r.yh = -a.xh; r.yl = -a.xl;
+  return r;
+}
+__device__ __forceinline__ dfc mul_plus_i(dfc a) {
+  dfc r;
+  r.xh = -a.yh; r.xl = -a.yl; r.yh = a.xh; r.yl = a.xl;
+  return r;
+}
 
 // split of a double into hi + lo floats (round to nearest each)
 __device__ __forceinline__ void df_split(double d, float& h, float& l) {
@@ -148,7 +195,11 @@ __device__ __forceinline__ dfc rot16(dfc d, int e) {
         default: c = -C1; s = S1; break;
       }
       // multiply by (c - i s) forward, (c + i s) inverse
-      const dfc w = INV ? dfc{df_hi(c), df_lo(c), df_hi(s), df_lo(s)} : dfc{df_hi(c), df_lo(c), df_hi(-s), df_lo(-s)};
+      dfc w;
+      w.xh = df_hi(c);
+      w.xl = df_lo(c);
+      w.yh = INV ? df_hi(s) : df_hi(-s);
+      w.yl = INV ? df_lo(s) : df_lo(-s);
       return cmul(d, w);
     }
   }

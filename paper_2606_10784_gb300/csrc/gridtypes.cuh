@@ -65,6 +65,7 @@ __device__ __forceinline__ float2 cto_vt(float2 v, double s) { return float2{v.x
 __device__ __forceinline__ double2 cto_vt(double2 v, double s) { return cto_d2(v, s); }
 __device__ __forceinline__ double2 cto_vt(dfc v, double s) { return cto_d2(v, s); }
 
+// tables of double-float values are float4 (xh, yh, xl, yl), the order of dfc
 __device__ __forceinline__ dfc ldro(const dfc* p) {
   const float4 v = __ldg(reinterpret_cast<const float4*>(p));
   return dfc{v.x, v.y, v.z, v.w};
@@ -78,8 +79,12 @@ __device__ __forceinline__ double2 shfl_pair(double2 v) {
   return double2{__shfl_xor_sync(0xffffffffu, v.x, 1), __shfl_xor_sync(0xffffffffu, v.y, 1)};
 }
 __device__ __forceinline__ dfc shfl_pair(dfc v) {
-  return dfc{__shfl_xor_sync(0xffffffffu, v.xh, 1), __shfl_xor_sync(0xffffffffu, v.xl, 1),
-             __shfl_xor_sync(0xffffffffu, v.yh, 1), __shfl_xor_sync(0xffffffffu, v.yl, 1)};
+  dfc r;
+  r.xh = __shfl_xor_sync(0xffffffffu, v.xh, 1);
+  r.yh = __shfl_xor_sync(0xffffffffu, v.yh, 1);
+  r.xl = __shfl_xor_sync(0xffffffffu, v.xl, 1);
+  r.yl = __shfl_xor_sync(0xffffffffu, v.yl, 1);
+  return r;
 }
 
 }  // namespace aim

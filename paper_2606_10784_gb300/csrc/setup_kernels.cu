@@ -146,7 +146,8 @@ __global__ void k_even_line_dft(double2* a, int H, int logP, const double2* tw, 
 
 __device__ __forceinline__ float4 split_df(double2 v) {
   const float xh = __double2float_rn(v.x), yh = __double2float_rn(v.y);
-  return float4{xh, __double2float_rn(v.x - (double)xh), yh, __double2float_rn(v.y - (double)yh)};
+  // the double-float order (xh, yh, xl, yl)
+  return float4{xh, yh, __double2float_rn(v.x - (double)xh), __double2float_rn(v.y - (double)yh)};
 }
 
 // The complex64 and double-float copies of FP64 values, rounded as k_pack_spectrum and the

@@ -448,8 +448,11 @@ __global__ void k_vcombine2_partial_df(const dfc* __restrict__ V, const dfc* __r
     df_add(b_ih, b_il, ph, pl, b_ih, b_il);
   }
   const size_t o = ((size_t)chunk * nrhs + r) * n + i;
-  part1[o] = dfc{a_rh, a_rl, a_ih, a_il};
-  part2[o] = dfc{b_rh, b_rl, b_ih, b_il};
+  dfc o1, o2;
+  o1.xh = a_rh; o1.xl = a_rl; o1.yh = a_ih; o1.yl = a_il;
+  o2.xh = b_rh; o2.xl = b_rl; o2.yh = b_ih; o2.yl = b_il;
+  part1[o] = o1;
+  part2[o] = o2;
 }
 
 // Stage 2: v_j = u / beta - V a1 into slot j (u is read there first), u_{j+1} = w / beta - kappa u -
