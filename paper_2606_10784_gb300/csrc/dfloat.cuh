@@ -165,24 +165,29 @@ __device__ __forceinline__ dfc rot16(dfc d, int e) {
     case 4: return INV ? mul_plus_i(d) : mul_minus_i(d);
     case 2:
     case 6: {
-      // W8 and W8^3 have |re| = |im| = 1/sqrt2: two sums and two scalings (24 FP32 operations)
-      // instead of a full complex product (32). With x + iy = d:
+      // W8 and W8^3 have |re| = |im| = 1/sqrt2: one paired sum and one paired scaling (the two
+      // lanes are the result's re and im) instead of a full complex product. With x + iy = d:
       //   forward e = 2: c (x + y) + i c (y - x)      inverse e = 2: c (x - y) + i c (x + y)
       //   forward e = 6: c (y - x) - i c (x + y)      inverse e = 6: -c (x + y) + i c (x - y)
+      // (a sum of negated parts is the negated sum, bit for bit, as is its scaling)
       constexpr float ch = df_hi(C2), cl = df_lo(C2);
-      float ph, pl, mh, ml;   // p = x + y, m = y - x (forward) or x - y (inverse)
-      df_add(d.xh, d.xl, d.yh, d.yl, ph, pl);
-      if (INV) df_add(d.xh, d.xl, -d.yh, -d.yl, mh, ml);
-      else df_add(d.yh, d.yl, -d.xh, -d.xl, mh, ml);
-      dfc r;
+      float2 ah, al, bh, bl;
       if (e == 2) {
-        if (INV) { df_scale(mh, ml, ch, cl, r.xh, r.xl); df_scale(ph, pl, ch, cl, r.yh, r.yl); }
-        else { df_scale(ph, pl, ch, cl, r.xh, r.xl); df_scale(mh, ml, ch, cl, r.yh, r.yl); }
+        if (INV) { ah = f2(d.xh, d.xh); al = f2(d.xl, d.xl); bh = f2(-d.yh, d.yh); bl = f2(-d.yl, d.yl); }
+        else { ah = f2(d.xh, d.yh); al = f2(d.xl, d.yl); bh = f2(d.yh, -d.xh); bl = f2(d.yl, -d.xl); }
       } else {
-        if (INV) { df_scale(ph, pl, -ch, -cl, r.xh, r.xl); df_scale(mh, ml, ch, cl, r.yh, r.yl); }
-        else { df_scale(mh, ml, ch, cl, r.xh, r.xl); df_scale(ph, pl, -ch, -cl, r.yh, r.yl); }
+        if (INV) { ah = f2(-d.xh, d.xh); al = f2(-d.xl, d.xl); bh = f2(-d.yh, -d.yh); bl = f2(-d.yl, -d.yl); }
+        else { ah = f2(d.yh, -d.xh); al = f2(d.yl, -d.xl); bh = f2(-d.xh, -d.yh); bl = f2(-d.xl, -d.yl); }
       }
-      return r;
+      float2 sh, sl;
+      df_add2(ah, al, bh, bl, sh, sl);
+      // df_scale on both lanes by (ch + cl)
+      const float2 c2 = f2(ch, ch), c2l = f2(cl, cl);
+      const float2 p = f2mul(sh, c2);
+      float2 er = f2fma(sh, c2, f2neg(p));
+      er = f2fma(sh, c2l, er);
+      er = f2fma(sl, c2, er);
+      return dfc{p.x, p.y, er.x, er.y};
     }
     default: {
       double c, s;

@@ -22,6 +22,9 @@ template <typename T2> __device__ __forceinline__ T2 cmul(T2 a, T2 b) {
 template <typename T2> __device__ __forceinline__ T2 cmulc(T2 a, T2 b) {
   return T2{a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
 }
+// complex64 sums and differences as one paired FP32 instruction each (both parts in one lane pair)
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
 template <typename T2> __device__ __forceinline__ T2 mul_minus_i(T2 a) { return T2{a.y, -a.x}; }
 template <typename T2> __device__ __forceinline__ T2 mul_plus_i(T2 a) { return T2{-a.y, a.x}; }
 
