@@ -25,6 +25,16 @@ template <typename T2> __device__ __forceinline__ T2 cmulc(T2 a, T2 b) {
 // complex64 sums and differences as one paired FP32 instruction each (both parts in one lane pair)
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+// complex64 products as a paired multiply and a paired fused multiply-add:
+// a b = ax (bx, by) + (-ay by, ay bx),  a conj(b) = ax (bx, -by) + (ay by, ay bx)
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  const float2 p = __fmul2_rn(make_float2(a.y, a.y), make_float2(b.y, b.x));
+  return __ffma2_rn(make_float2(a.x, a.x), b, make_float2(-p.x, p.y));
+}
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  const float2 p = __fmul2_rn(make_float2(a.y, a.y), make_float2(b.y, b.x));
+  return __ffma2_rn(make_float2(a.x, a.x), make_float2(b.x, -b.y), p);
+}
 template <typename T2> __device__ __forceinline__ T2 mul_minus_i(T2 a) { return T2{a.y, -a.x}; }
 template <typename T2> __device__ __forceinline__ T2 mul_plus_i(T2 a) { return T2{-a.y, a.x}; }
 
