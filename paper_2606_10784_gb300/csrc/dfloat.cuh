@@ -125,6 +125,14 @@ __device__ __forceinline__ dfc cmulc(dfc a, dfc b) {
   return dfc{rh.x, rh.y, rl.x, rl.y};
 }
 
+// conj(a) * b = (ax bx + ay by) + i(ax by - ay bx): lane 0 ax bx + ay by, lane 1 ax by + (-ay) bx
+__device__ __forceinline__ dfc cconjmul(dfc a, dfc b) {
+  float2 rh, rl;
+  df_dot2_2(f2(a.xh, a.xh), f2(a.xl, a.xl), f2(b.xh, b.yh), f2(b.xl, b.yl), f2(a.yh, -a.yh), f2(a.yl, -a.yl),
+            f2(b.yh, b.xh), f2(b.yl, b.xl), rh, rl);
+  return dfc{rh.x, rh.y, rl.x, rl.y};
+}
+
 __device__ __forceinline__ dfc mul_minus_i(dfc a) {
   dfc r;
   r.xh = a.yh; r.xl = a.yl; r.yh = -a.xh; r.yl = -a.xl;

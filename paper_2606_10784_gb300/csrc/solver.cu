@@ -222,23 +222,15 @@ __global__ void k_multidot2_partial_df(const dfc* __restrict__ V, const dfc* __r
   const dfc* v = V + ((size_t)l * nrhs + r) * n;
   const dfc* x0 = R0 + (size_t)r * n;
   const dfc* x1 = R1 != nullptr ? R1 + (size_t)r * n : nullptr;
-  float a_rh = 0.f, a_rl = 0.f, a_ih = 0.f, a_il = 0.f;
-  float b_rh = 0.f, b_rl = 0.f, b_ih = 0.f, b_il = 0.f;
+  // products and sums as paired instructions on the (re, im) lanes (cconjmul, cadd)
+  dfc acc0 = dfc{0.f, 0.f, 0.f, 0.f}, acc1 = dfc{0.f, 0.f, 0.f, 0.f};
   for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    const dfc a = v[i], b = x0[i];
-    float ph, pl;
-    df_dot2<+1>(a.xh, a.xl, b.xh, b.xl, a.yh, a.yl, b.yh, b.yl, ph, pl);
-    df_add(a_rh, a_rl, ph, pl, a_rh, a_rl);
-    df_dot2<-1>(a.xh, a.xl, b.yh, b.yl, a.yh, a.yl, b.xh, b.xl, ph, pl);
-    df_add(a_ih, a_il, ph, pl, a_ih, a_il);
-    if (x1 != nullptr) {
-      const dfc c = x1[i];
-      df_dot2<+1>(a.xh, a.xl, c.xh, c.xl, a.yh, a.yl, c.yh, c.yl, ph, pl);
-      df_add(b_rh, b_rl, ph, pl, b_rh, b_rl);
-      df_dot2<-1>(a.xh, a.xl, c.yh, c.yl, a.yh, a.yl, c.xh, c.xl, ph, pl);
-      df_add(b_ih, b_il, ph, pl, b_ih, b_il);
-    }
+    const dfc a = v[i];
+    acc0 = cadd(acc0, cconjmul(a, x0[i]));
+    if (x1 != nullptr) acc1 = cadd(acc1, cconjmul(a, x1[i]));
   }
+  float a_rh = acc0.xh, a_rl = acc0.xl, a_ih = acc0.yh, a_il = acc0.yl;
+  float b_rh = acc1.xh, b_rl = acc1.xl, b_ih = acc1.yh, b_il = acc1.yl;
   __shared__ float s8[32][8];
   warp_sum_df(a_rh, a_rl, a_ih, a_il);
   warp_sum_df(b_rh, b_rl, b_ih, b_il);
@@ -431,28 +423,17 @@ __global__ void k_vcombine2_partial_df(const dfc* __restrict__ V, const dfc* __r
   const int chunk = blockIdx.y, r = blockIdx.z;
   if (i >= n) return;
   const int j0 = chunk * kCgsChunk, j1 = min(J, j0 + kCgsChunk);
-  float a_rh = 0.f, a_rl = 0.f, a_ih = 0.f, a_il = 0.f;
-  float b_rh = 0.f, b_rl = 0.f, b_ih = 0.f, b_il = 0.f;
+  // products and sums as paired instructions on the (re, im) lanes (cmul, cadd)
+  dfc acc1 = dfc{0.f, 0.f, 0.f, 0.f}, acc2 = dfc{0.f, 0.f, 0.f, 0.f};
 #pragma unroll 4
   for (int l = j0; l < j1; ++l) {
     const dfc v = V[((size_t)l * nrhs + r) * n + i];
-    const dfc h = a1[(size_t)l * nrhs + r], k = g[(size_t)l * nrhs + r];
-    float ph, pl;
-    df_dot2<-1>(v.xh, v.xl, h.xh, h.xl, v.yh, v.yl, h.yh, h.yl, ph, pl);
-    df_add(a_rh, a_rl, ph, pl, a_rh, a_rl);
-    df_dot2<+1>(v.xh, v.xl, h.yh, h.yl, v.yh, v.yl, h.xh, h.xl, ph, pl);
-    df_add(a_ih, a_il, ph, pl, a_ih, a_il);
-    df_dot2<-1>(v.xh, v.xl, k.xh, k.xl, v.yh, v.yl, k.yh, k.yl, ph, pl);
-    df_add(b_rh, b_rl, ph, pl, b_rh, b_rl);
-    df_dot2<+1>(v.xh, v.xl, k.yh, k.yl, v.yh, v.yl, k.xh, k.xl, ph, pl);
-    df_add(b_ih, b_il, ph, pl, b_ih, b_il);
+    acc1 = cadd(acc1, cmul(v, a1[(size_t)l * nrhs + r]));
+    acc2 = cadd(acc2, cmul(v, g[(size_t)l * nrhs + r]));
   }
   const size_t o = ((size_t)chunk * nrhs + r) * n + i;
-  dfc o1, o2;
-  o1.xh = a_rh; o1.xl = a_rl; o1.yh = a_ih; o1.yl = a_il;
-  o2.xh = b_rh; o2.xl = b_rl; o2.yh = b_ih; o2.yl = b_il;
-  part1[o] = o1;
-  part2[o] = o2;
+  part1[o] = acc1;
+  part2[o] = acc2;
 }
 
 // Stage 2: v_j = u / beta - V a1 into slot j (u is read there first), u_{j+1} = w / beta - kappa u -
