@@ -61,7 +61,7 @@ E2E_STEPS_MAX = 5
 # ncu capture of the current kernel and default schedule at the single-solve size; the capture and
 # its command are in profiles/col_conv_*_single_solve_n10000.md. None where no capture of the
 # current kernel exists.
-COL_CONV_TRAFFIC = {"fp64": 534464256, "mixed": 202545664, "native": None}
+COL_CONV_TRAFFIC = {"fp64": 533945856, "mixed": 201229440, "native": None}
 
 
 def parse():
