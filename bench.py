@@ -87,6 +87,11 @@ def parse():
     ap.add_argument("--op", default="N", help="profile case: operator")
     ap.add_argument("--repeat", type=int, default=1, help="profile case: products")
     ap.add_argument("--time", action="store_true", help="profile case: print mean ms per launch of each kernel")
+    ap.add_argument("--dft-stage", action="store_true",
+                    help="time one radix-16 DFT pass on CUDA cores and on tensor cores (aim_dft_stage)")
+    ap.add_argument("--stage-groups", type=int, default=152 * 32, help="dft stage: CTAs of 4096 complex64 values")
+    ap.add_argument("--stage-passes", type=int, default=256, help="dft stage: passes per launch")
+    ap.add_argument("--stage-variant", type=int, default=-1, help="dft stage: time only this variant (0, 1, 2)")
     return ap.parse_args()
 
 
@@ -637,9 +642,109 @@ def profile_case(args):
     return out
 
 
+# --------------------------------------------------------------------------------------
+# DFT stage on CUDA cores against tensor cores
+# --------------------------------------------------------------------------------------
+STAGE_VARIANTS = (("cuda_cores_fp32", 0), ("mma_tf32", 1), ("mma_tf32x3", 2), ("split_data_path_only", 3))
+# the dense contraction of one DFT-16 column: 2 x 32 x 32 real flops
+GEMM16_FLOPS = 2 * 32 * 32
+
+
+def dft_stage_case(args):
+    """Times aim_dft_stage: `--stage-passes` radix-16 passes over `--stage-groups` groups of 4096
+    complex64 values held in shared memory, for each variant (the product's CUDA-core butterfly,
+    mma.sync TF32, mma.sync split TF32). The rate is taken from the difference between launches of
+    `--stage-passes` and half as many passes, so loads, stores and set-up cancel. Beside it: the tensor cores' TF32 rate measured by
+    cuBLAS on a large GEMM, and the DFT-16 rate that rate would give a tcgen05 stage that spent
+    nothing on data movement (2 x 32 x 32 flops per column, three products with the split).
+    Accuracy: relative L2 error of one pass against the FP64 definition on two groups."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2606_10784_gb300 import aim
+    G, passes = args.stage_groups, args.stage_passes
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    x = torch.complex(torch.randn(G * 4096, device="cuda", generator=gen),
+                      torch.randn(G * 4096, device="cuda", generator=gen))
+    y = torch.empty_like(x)
+    st = torch.cuda.current_stream()
+
+    def timed(v, p, reps=7):
+        for _ in range(3):
+            aim.dft_stage(v, x, y, p, stream=st)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            aim.dft_stage(v, x, y, p, stream=st)
+            e1.record(st)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    # FP64 reference of one pass on the first two groups (the definition in aim.h)
+    x2 = x[:2 * 4096].cpu().numpy().astype(np.complex128)
+    cols = x2.reshape(2, 16, 256).transpose(0, 2, 1)
+    c, i = np.arange(256)[:, None], np.arange(16)[None, :]
+    t = np.exp(-2j * np.pi * (c % 16) * i / 256) / 4
+    F = np.exp(-2j * np.pi * np.outer(np.arange(16), np.arange(16)) / 16)
+    ref = np.einsum("gci,ki->gck", cols * t[None], F).reshape(-1)
+    out = {"case": "radix-16 DFT pass, %d groups x 4096 complex64 values in shared memory, %d passes per launch"
+                   % (G, passes), "variants": {}}
+    ref_split = (cols * t[None]).transpose(0, 2, 1).reshape(-1)   # variant 3: t(c, i) x_i(c) in place
+    for name, v in STAGE_VARIANTS:
+        if args.stage_variant >= 0 and v != args.stage_variant:
+            continue
+        half = passes // 2
+        ms_p, ms_h = timed(v, passes), timed(v, half)
+        rate = G * 256 * (passes - half) / ((ms_p - ms_h) * 1e-3)
+        aim.dft_stage(v, x[:2 * 4096], y[:2 * 4096], 1, stream=st)
+        torch.cuda.synchronize()
+        want = ref_split if v == 3 else ref
+        err = float(np.linalg.norm(y[:2 * 4096].cpu().numpy() - want) / np.linalg.norm(want))
+        out["variants"][name] = {"ms_launch": round(ms_p, 4), "ms_launch_half_passes": round(ms_h, 4),
+                                 "dft16_per_s": rate, "rel_err_one_pass": err}
+    if "cuda_cores_fp32" not in out["variants"]:
+        return out
+    base = out["variants"]["cuda_cores_fp32"]["dft16_per_s"]
+    for name in out["variants"]:
+        out["variants"][name]["vs_cuda_cores"] = out["variants"][name]["dft16_per_s"] / base
+    # tensor-core TF32 rate by cuBLAS (tcgen05 inside the library), burst
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    n = 8192
+    a = torch.randn(n, n, device="cuda", generator=gen)
+    b = torch.randn(n, n, device="cuda", generator=gen)
+    for _ in range(3):
+        torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = float("inf")
+    for _ in range(10):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    tf32 = 2.0 * n ** 3 / (best * 1e-3) / 1e12
+    out["tensor_core_bound"] = {
+        "tf32_gemm_tflops_cublas": tf32,
+        "dft16_per_s_tf32": tf32 * 1e12 / GEMM16_FLOPS,
+        "dft16_per_s_split_tf32": tf32 * 1e12 / (3 * GEMM16_FLOPS),
+        "note": "a tcgen05 stage at the measured TF32 GEMM rate with no data movement, operand split or "
+                "twiddle cost: the most any tensor-core DFT-16 stage could reach"}
+    out["bound_vs_cuda_cores"] = {"tf32": out["tensor_core_bound"]["dft16_per_s_tf32"] / base,
+                                  "split_tf32": out["tensor_core_bound"]["dft16_per_s_split_tf32"] / base}
+    return out
+
+
 def main():
     args = parse()
-    if args.profile_case:
+    if args.dft_stage:
+        out = dft_stage_case(args)
+    elif args.profile_case:
         out = profile_case(args)
     elif args.impl == "reference":
         out = reference_arm(args)

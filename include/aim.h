@@ -415,6 +415,34 @@ aim_status aim_query_solve_bytes(const aim_geometry* geometry, const aim_grid* g
                                  const aim_stencil* stencil, int nrhs, const aim_solve_opts* opts,
                                  size_t* bytes);
 
+/* One radix-16 pass of a batch of DFTs, on CUDA cores or on tensor cores (no counterpart in the
+ * paper; for measurement). It answers whether the DFT stages of the grid product (Eq. 8 / Eq. 10)
+ * should run on tensor cores: written as a dense contraction, the DFT-16 of one complex column is
+ * the 32 x 32 real matrix [C S; -S C] (C = cos(2 pi k i/16), S = sin(2 pi k i/16)) times its 32
+ * real and imaginary parts. Each CTA loads 4096 complex64 values of x, applies `passes` passes
+ * to them in shared memory, and stores the result to y. A pass maps element i of column c (value
+ * c + 256 i) to output k of column c (value 16 c + k):
+ *     X_k(c) = sum_i x_i(c) t(c, i) exp(-2 pi j k i/16),  t(c, i) = exp(-2 pi j (c mod 16) i/256)/4.
+ * variant: AIM_DFT_STAGE_CUDA_CORES (the product's register butterfly, FP32),
+ *          AIM_DFT_STAGE_MMA_TF32 (mma.sync TF32, one product per term; the tensor core reads the
+ *          top 19 bits of the FP32 data),
+ *          AIM_DFT_STAGE_MMA_TF32X3 (mma.sync with the data split as hi = top 19 bits,
+ *          lo = x - hi, and a_hi b_hi + a_hi b_lo + a_lo b_hi),
+ *          AIM_DFT_STAGE_SPLIT_ONLY (the split variant's loads, twiddles, data split and stores
+ *          without the products: each pass stores hi + lo = t(c, i) x_i(c) at value c + 256 i;
+ *          its rate bounds any tensor-core pass fed from registers).
+ * x, y: device pointers (current device), groups * 4096 interleaved complex64 values each,
+ * 8-byte aligned; they may be the same buffer. groups in [1, 2^20], passes in [0, 2^20].
+ * Returns AIM_EINVAL for a bad variant, size or pointer, before any launch. */
+typedef enum {
+  AIM_DFT_STAGE_CUDA_CORES = 0,
+  AIM_DFT_STAGE_MMA_TF32 = 1,
+  AIM_DFT_STAGE_MMA_TF32X3 = 2,
+  AIM_DFT_STAGE_SPLIT_ONLY = 3
+} aim_dft_stage_variant;
+
+aim_status aim_dft_stage(int variant, int groups, int passes, const void* x, void* y, void* stream);
+
 /* Launch accounting and kernel timing (no counterpart in the paper; for measurement).
  * aim_launch_count: kernels the library has enqueued in this process so far (all contexts).
  * aim_profile_start: from now on every launch is bracketed by two CUDA events recorded on

@@ -25,6 +25,8 @@ TM, TE = 0, 1
 FP64, MIXED, FP64_NATIVE = 0, 1, 2
 FILTER_NONE, FILTER_NUMERICAL, FILTER_ANALYTIC = 0, 1, 2
 TABLE_SPECTRUM, TABLE_SPECTRUM_FILTERED, TABLE_ANALYTIC_SAMPLES, TABLE_ANALYTIC_SPECTRUM = 0, 1, 2, 3
+DFT_STAGE_CUDA_CORES, DFT_STAGE_MMA_TF32, DFT_STAGE_MMA_TF32X3, DFT_STAGE_SPLIT_ONLY = 0, 1, 2, 3
+DFT_STAGE_GROUP = 4096   # complex64 values per CTA of aim_dft_stage
 
 OPS = {"S": OP_S, "S_alpha": OP_S_ALPHA, "N": OP_N, "calderon": OP_CALDERON,
        "calderon_alpha": OP_CALDERON_ALPHA, "gram_inv": OP_GRAM_INV, "efie": OP_EFIE, "efie_alpha": OP_EFIE_ALPHA,
@@ -174,6 +176,8 @@ def lib() -> ctypes.CDLL:
     L.aim_status_str.restype = ctypes.c_char_p
     L.aim_last_error.argtypes = []
     L.aim_last_error.restype = ctypes.c_char_p
+    L.aim_dft_stage.argtypes = [i, i, i, vp, vp, vp]
+    L.aim_dft_stage.restype = i
     _lib = L
     return L
 
@@ -190,6 +194,17 @@ def matvec_multi(ctxs, ops, xs, ys, precision: int = FP64, stream=None):
     _check(lib().aim_matvec_multi(count, arr_c, arr_o, arr_r, arr_x, arr_y, int(precision), _stream_ptr(stream)),
            "aim_matvec_multi")
     return ys
+
+
+def dft_stage(variant: int, x, y, passes: int, stream=None):
+    """`passes` radix-16 DFT passes over each group of 4096 complex64 values of x, into y
+    (aim_dft_stage: a measurement of the stage on CUDA cores or tensor cores); x, y: contiguous
+    complex64 device tensors whose size is a multiple of 4096."""
+    if x.numel() != y.numel() or x.numel() % DFT_STAGE_GROUP:
+        raise ValueError("x and y must hold the same multiple of %d values" % DFT_STAGE_GROUP)
+    _check(lib().aim_dft_stage(int(variant), x.numel() // DFT_STAGE_GROUP, int(passes), _ptr(x), _ptr(y),
+                               _stream_ptr(stream)), "aim_dft_stage")
+    return y
 
 
 class Batcher:

@@ -17,7 +17,8 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libaimgb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["capi.cu", "setup_host.cpp", "setup_kernels.cu", "matvec_common.cu", "matvec_dfc.cu", "matvec_f32.cu",
-           "matvec_f64.cu", "solver.cu", "prof.cu", "noalloc.cu", "lanczos.cu", "batcher.cu", "setup_cache.cu"]
+           "matvec_f64.cu", "solver.cu", "prof.cu", "noalloc.cu", "lanczos.cu", "batcher.cu", "setup_cache.cu",
+           "dft_stage.cu"]
 
 
 def nvcc() -> str:

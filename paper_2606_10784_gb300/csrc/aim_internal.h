@@ -46,7 +46,7 @@ aim_status check_device(const aim_ctx* ctx);
 enum KernelId {
   K_ROW_FWD = 0, K_COL_CONV, K_ROW_INV, K_GATHER, K_GRAM,
   K_SETUP_SAMPLE, K_SETUP_DFT, K_SETUP_PACK, K_SETUP_SEGPAIRS, K_SETUP_NEAR,
-  K_RHS, K_GMRES, K_MULTI, K_COUNT
+  K_RHS, K_GMRES, K_MULTI, K_DFT_STAGE, K_COUNT
 };
 void count_launches(int id, int n);   // counted, not timed
 void thread_launch_counts(long long* out);   // this host thread's counts, K_COUNT entries

@@ -22,6 +22,7 @@ static const char* kKernelNames[K_COUNT] = {
     "rhs_planewave",
     "gmres_arnoldi (DCGS2 projections and updates; timed per step)",
     "grid_multi (persistent: row passes, column pass and gathers of several contexts)",
+    "dft_stage (radix-16 pass measurement: CUDA cores or tensor cores)",
 };
 
 namespace {

@@ -133,6 +133,10 @@ def test_new_entry_points_reject_bad_arguments_before_the_gpu(lib):
     assert lib.aim_lanczos_bidiag(None, 0, 4, 0, None, a, a, None, None, None) == aim.EINVAL
     assert lib.aim_matvec_multi(0, None, None, None, None, None, 0, None) == aim.EINVAL
     assert lib.aim_matvec_multi(33, None, None, None, None, None, 0, None) == aim.EINVAL
+    assert lib.aim_dft_stage(4, 1, 1, None, None, None) == aim.EINVAL
+    assert lib.aim_dft_stage(0, 0, 1, None, None, None) == aim.EINVAL
+    assert lib.aim_dft_stage(0, 1, -1, None, None, None) == aim.EINVAL
+    assert lib.aim_dft_stage(2, 1, 1, None, None, None) == aim.EINVAL
     lib.aim_batcher_destroy(None)        # NULL is allowed
 
 
