@@ -212,47 +212,48 @@ __host__ __device__ __forceinline__ size_t hess_index(int l, int m) { return (si
 __host__ __device__ __forceinline__ size_t hess_entries(int restart) { return (size_t)restart * (restart + 3) / 2; }
 
 // part0[(z J + l) nrhs + r] = sum over chunk z of conj(V[l][r][i]) R0[r][i]; part1 likewise with
-// R1 (not written when R1 is null): both projections over one read of the basis (one basis
-// vector per block: four per block, sharing the loads of R0 and R1, ran 30 % slower at 3 CTAs
-// per SM instead of 6)
-__global__ void k_multidot2_partial_df(const dfc* __restrict__ V, const dfc* __restrict__ R0, const dfc* __restrict__ R1,
-                                       int n, int nrhs, int J, double2* __restrict__ part0, double2* __restrict__ part1) {
-  const int l = blockIdx.x, r = blockIdx.y, z = blockIdx.z;
+// R1 (not written when R1 is null): both projections over one read of the basis. One warp per
+// (basis vector, chunk): each lane sums every 32nd element of the chunk (64 of them), then a fixed
+// shuffle tree adds the lanes, so the reduction is a small part of a warp's work. A block's eight
+// warps take eight consecutive basis vectors over the same chunk, so they read the same R0 and R1
+// elements at about the same time and all but the first find them in L1. (One warp per block and
+// eight elements per thread before a block-wide reduction ran at 2.5 TB/s of basis reads.)
+constexpr int kDot2Warps = 8;
+
+__global__ void __launch_bounds__(32 * kDot2Warps) k_multidot2_partial_df(const dfc* __restrict__ V,
+                                                                          const dfc* __restrict__ R0,
+                                                                          const dfc* __restrict__ R1, int n, int nrhs,
+                                                                          int J, double2* __restrict__ part0,
+                                                                          double2* __restrict__ part1) {
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int l = blockIdx.x * kDot2Warps + wid, r = blockIdx.y, z = blockIdx.z;
+  if (l >= J) return;   // whole warps; the kernel has no block-wide barrier
   const int i0 = z * kDotChunk, i1 = min(n, i0 + kDotChunk);
   const dfc* v = V + ((size_t)l * nrhs + r) * n;
   const dfc* x0 = R0 + (size_t)r * n;
   const dfc* x1 = R1 != nullptr ? R1 + (size_t)r * n : nullptr;
   // products and sums as paired instructions on the (re, im) lanes (cconjmul, cadd)
   dfc acc0 = dfc{0.f, 0.f, 0.f, 0.f}, acc1 = dfc{0.f, 0.f, 0.f, 0.f};
-  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-    const dfc a = v[i];
-    acc0 = cadd(acc0, cconjmul(a, x0[i]));
-    if (x1 != nullptr) acc1 = cadd(acc1, cconjmul(a, x1[i]));
+  if (x1 != nullptr) {
+#pragma unroll 4
+    for (int i = i0 + lane; i < i1; i += 32) {
+      const dfc a = v[i];
+      acc0 = cadd(acc0, cconjmul(a, x0[i]));
+      acc1 = cadd(acc1, cconjmul(a, x1[i]));
+    }
+  } else {
+#pragma unroll 4
+    for (int i = i0 + lane; i < i1; i += 32) acc0 = cadd(acc0, cconjmul(v[i], x0[i]));
   }
   float a_rh = acc0.xh, a_rl = acc0.xl, a_ih = acc0.yh, a_il = acc0.yl;
-  float b_rh = acc1.xh, b_rl = acc1.xl, b_ih = acc1.yh, b_il = acc1.yl;
-  __shared__ float s8[32][8];
   warp_sum_df(a_rh, a_rl, a_ih, a_il);
-  warp_sum_df(b_rh, b_rl, b_ih, b_il);
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    s8[wid][0] = a_rh; s8[wid][1] = a_rl; s8[wid][2] = a_ih; s8[wid][3] = a_il;
-    s8[wid][4] = b_rh; s8[wid][5] = b_rl; s8[wid][6] = b_ih; s8[wid][7] = b_il;
-  }
-  __syncthreads();
-  if (wid == 0) {
-    const int nw = blockDim.x >> 5;
-    const bool in = lane < nw;
-    a_rh = in ? s8[lane][0] : 0.f; a_rl = in ? s8[lane][1] : 0.f; a_ih = in ? s8[lane][2] : 0.f; a_il = in ? s8[lane][3] : 0.f;
-    b_rh = in ? s8[lane][4] : 0.f; b_rl = in ? s8[lane][5] : 0.f; b_ih = in ? s8[lane][6] : 0.f; b_il = in ? s8[lane][7] : 0.f;
-    warp_sum_df(a_rh, a_rl, a_ih, a_il);
+  const size_t o = ((size_t)z * J + l) * nrhs + r;
+  if (x1 != nullptr) {
+    float b_rh = acc1.xh, b_rl = acc1.xl, b_ih = acc1.yh, b_il = acc1.yl;
     warp_sum_df(b_rh, b_rl, b_ih, b_il);
-    if (lane == 0) {
-      const size_t o = ((size_t)z * J + l) * nrhs + r;
-      part0[o] = to_d2(a_rh, a_rl, a_ih, a_il);
-      if (part1 != nullptr) part1[o] = to_d2(b_rh, b_rl, b_ih, b_il);
-    }
+    if (lane == 0) part1[o] = to_d2(b_rh, b_rl, b_ih, b_il);
   }
+  if (lane == 0) part0[o] = to_d2(a_rh, a_rl, a_ih, a_il);
 }
 
 // D0[l nrhs + r], D1[...] = chunk sums in chunk order (FP64), D0's double-float copy, and the
@@ -437,9 +438,9 @@ __global__ void k_vcombine2_partial_df(const dfc* __restrict__ V, const dfc* __r
 }
 
 // Stage 2: v_j = u / beta - V a1 into slot j (u is read there first), u_{j+1} = w / beta - kappa u -
-// V g into slot j+1 and, in binary64, into cur (the next product's input). Four adjacent threads
-// per element sum every fourth chunk; a fixed shuffle tree adds their sums.
-constexpr int kFinishLanes = 4;
+// V g into slot j+1 and, in binary64, into cur (the next product's input). Eight adjacent threads
+// per element sum every eighth chunk; a fixed shuffle tree adds their sums.
+constexpr int kFinishLanes = 8;
 
 __global__ void k_vcombine2_finish_df(const dfc* __restrict__ part1, const dfc* __restrict__ part2, int nchunks, int n,
                                       int nrhs, const double2* __restrict__ scal, dfc* __restrict__ Vj,
@@ -797,7 +798,7 @@ static aim_status gmres_core(aim_ctx* ctx, aim_op op, int precision, int nrhs, c
         k_to_dfc<<<nb, tpb, 0, st>>>(ws.w, (int)vsz, ws.wdf);
       }
       count_launches(K_GMRES, 3);
-      k_multidot2_partial_df<<<dim3(J, nrhs, nz), 256, 0, st>>>(
+      k_multidot2_partial_df<<<dim3((J + kDot2Warps - 1) / kDot2Warps, nrhs, nz), 32 * kDot2Warps, 0, st>>>(
           ws.V, Vj, final_step ? nullptr : ws.wdf, n, nrhs, J, part0, final_step ? nullptr : part1);
       k_dcgs2_finish<<<blocks_for((long long)J * nrhs, tpb), tpb, 0, st>>>(part0, final_step ? nullptr : part1, nz, J,
                                                                           nrhs, j, restart, ws.dots, ws.dots2,
