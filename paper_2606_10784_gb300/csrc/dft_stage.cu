@@ -8,8 +8,8 @@
 //         [ -S  C ]
 // times the column's 32 reals, so a batch of n columns is one (32 x 32) x (32 x n) product that
 // tensor cores execute. These kernels run one pass of the transforms -- twiddle, DFT-16, exchange
-// through shared memory -- in three ways, on data that stays in shared memory for many passes, so
-// that the stage's own throughput is measured, not HBM:
+// through shared memory -- in four variants, on data that stays in shared memory for many passes,
+// so that the stage's own throughput is measured, not HBM:
 //   variant 0: the product's register butterfly (dft_reg<16>) with paired FP32 complex products;
 //   variant 1: mma.sync m16n8k8 with TF32 operands, one product per term: the FP32 data go in as
 //              they are and the tensor core reads their top 19 bits (about 2^-10 relative error
@@ -25,7 +25,7 @@
 //   element i of column c is value c + 256 i; output k of column c is value 16 c + k;
 //   X_k(c) = sum_i x_i(c) t(c, i) exp(-2 pi j k i/16),  t(c, i) = exp(-2 pi j (c mod 16) i/256)/4.
 // The factor 1/4 keeps repeated passes at the inputs' scale. Each thread's twiddles do not change
-// from pass to pass, so both variants hold them in registers; the product reads them from the
+// from pass to pass, so every variant holds them in registers; the product reads them from the
 // twiddle table instead, at the same cost for any butterfly.
 #include <cuda_runtime.h>
 
