@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-sub", action="store_true", help="skip the mixed / batching / serving sub-results")
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--workload", choices=["single", "batching", "serving"], default="single",
+    ap.add_argument("--workload", choices=["single", "batching", "serving", "multi"], default="single",
                     help="single: one filtered Calderon solve per step (the default line, with sub-results); "
                          "batching / serving: that sub-result alone as its own line")
     ap.add_argument("--requests", type=int, default=40, help="serving: timed requests (after 10%% warm-up)")
@@ -609,6 +609,60 @@ def serving_arm(args, aim=None):
                                  "run in one multi-context launch per stage"}}
 
 
+def multi_arm(args, aim=None, rounds=20):
+    """Several problems in one launch: filtered Calderon products of 8 contexts drawn from the serving
+    stream (seed 11, each with its own nrhs plane-wave-sized random vectors), one round = one product
+    of each. Timed both ways on one stream with CUDA events after one warm-up round: a separate
+    aim_matvec per context, and aim_matvec_multi (every grid-pass stage of all eight in one
+    persistent launch). Mixes: the first 8 requests with P <= 512, the first 8 with 512 <= P <= 1024,
+    and the stream's first 8; in mixed precision and FP64."""
+    import torch
+    if aim is None:
+        import __graft_entry__
+        __graft_entry__.build()
+        from paper_2606_10784_gb300 import aim
+    stream = synth.serving_stream(200, rate=200.0, seed=11)
+    mixes = {"P<=512": lambda P: P <= 512, "512<=P<=1024": lambda P: 512 <= P <= 1024, "first 8": lambda P: True}
+    st = solve_stream()
+    out = {"metric": "filtered Calderon products of 8 contexts per round: ms per round", "unit": "ms", "rounds": rounds,
+           "mixes": {}}
+    for name, keep in mixes.items():
+        ctxs, xs, ys = [], [], []
+        for s in stream:
+            if len(ctxs) == 8:
+                break
+            if not keep(max(2 * s.m, 64)):   # the embedding side aim_setup selects for m (a power of two)
+                continue
+            nodes = synth.StarContour.from_seed(s.seed % 100000).polygon(s.perimeter, s.n_seg)
+            ctxs.append(aim.Context(nodes, s.k, aim.TE, s.m, alpha=s.alpha, stream=st))
+            x = torch.from_numpy(synth.random_coeffs(s.n_seg, s.nrhs, seed=len(ctxs))).cuda()
+            xs.append(x)
+            ys.append(torch.empty_like(x))
+        row = {"fft_P": sorted({c.info()["fft_P"] for c in ctxs}), "nrhs": [int(x.shape[0]) for x in xs]}
+        for pname, prec in (("mixed", aim.MIXED), ("fp64", aim.FP64)):
+            def separate():
+                for c, x, y in zip(ctxs, xs, ys):
+                    c.matvec("calderon_alpha", x, y, precision=prec, stream=st)
+
+            def fused():
+                aim.matvec_multi(ctxs, ["calderon_alpha"] * len(ctxs), xs, ys, precision=prec, stream=st)
+
+            for label, fn in (("separate", separate), ("multi", fused)):
+                fn()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                for _ in range(rounds):
+                    fn()
+                e1.record(st)
+                torch.cuda.synchronize()
+                row["%s_%s_ms" % (pname, label)] = e0.elapsed_time(e1) / rounds
+        out["mixes"][name] = row
+        for c in ctxs:
+            c.close()
+    return out
+
+
 # --------------------------------------------------------------------------------------
 # profiling case (for ncu): one operator of the single-solve workload
 # --------------------------------------------------------------------------------------
@@ -752,6 +806,8 @@ def main():
         out = batching_arm(args)
     elif args.workload == "serving":
         out = serving_arm(args)
+    elif args.workload == "multi":
+        out = multi_arm(args)
     else:
         out = gb300_arm(args)
     if out is not None:
